@@ -1,0 +1,351 @@
+"""Benchmark of the batched QP projection (projected trajectories/s, p99 latency).
+
+One step = one prism_proj_solve of one MPC-step batch: N=4096 samples x J=12
+joints, H=50, dt=0.02, 100 iterations (ADMM, row-normalised, FP32), inputs
+already resident in HBM.  64 distinct step inputs (629 MB, more than the 126 MB
+L2) are cycled, so every timed step reads inputs that are not in L2.
+
+Prints one JSON line (rank 0).  Under torchrun (N>1) every rank projects its
+own independent batches (weak scaling, no collective on the data path); the
+time is the max over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2608_25666_b300 import workloads  # noqa: E402
+
+WORKLOAD = workloads.WORKLOADS["realistic"]
+METRIC = "projected trajectories/s"
+UNIT = "trajectories/s"
+N_INPUTS = 64
+
+
+def flops_per_column_iteration(H: int) -> int:
+    """Algorithmic FP32 flops of one iteration of one column (ADMM mode).
+
+    Counted from the method, not from the padded kernel:
+      y = Fh x                      3H - 3   (cumsum, first and second differences)
+      slack clip + multiplier       6 (4H-1) (w = 2y - t, clip, t = z - y + t)
+      row weights                   4H - 1
+      Fh^T s                        8H - 5   (suffix sum, differences, block sum)
+      rhs = xi + rho g              2 (H-1)
+      K-apply on x_2..x_H           2 (H-1)^2 + 2 (H-1)   (kb v0 term)
+    """
+    return 2 * (H - 1) ** 2 + 43 * H - 19
+
+
+def peak_fp32_tflops(num_sms: int, mhz: float) -> float:
+    """FP32 FMA issue rate: SMs x 128 lanes x 2 flop x clock."""
+    return num_sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"prism_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == 7:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier_max(ws, value: float) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_sample(seconds_target: float = 15.0, rank_step: int = 0):
+    """The oracle as it stands on the host cores, on a bounded column sample
+    of one step of the workload; returns (trajectories/s, cores, description)."""
+    import oracle
+    w = WORKLOAD
+    cores = os.cpu_count() or 1
+    b = workloads.make_batch(w, step=rank_step)
+    rng = np.random.default_rng(0)
+    # calibrate on a small sample, then size the sample for ~seconds_target
+    ncal = max(cores * 16, 64)
+    cols = rng.choice(w.N * w.J, ncal, replace=False)
+    t0 = time.perf_counter()
+    oracle.solve_batch(b["xi"], b["q0"], b["v0"], b["bounds"], w.dt, w.iters, w.rho, cols=cols,
+                       nthreads=cores)
+    per_col = (time.perf_counter() - t0) / ncal
+    ncols = int(min(w.N * w.J, max(ncal, seconds_target / max(per_col, 1e-9))))
+    cols = rng.choice(w.N * w.J, ncols, replace=False)
+    t0 = time.perf_counter()
+    oracle.solve_batch(b["xi"], b["q0"], b["v0"], b["bounds"], w.dt, w.iters, w.rho, cols=cols,
+                       nthreads=cores)
+    dt = time.perf_counter() - t0
+    traj_per_s = (ncols / w.J) / dt
+    desc = (f"{ncols} random columns (= {ncols / w.J:.1f} trajectories) of one {w.N}x{w.J}x{w.H} "
+            f"step, {w.iters} iterations, {dt:.1f} s, OpenMP over columns")
+    return traj_per_s, cores, desc
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    per_step = []
+    cores = os.cpu_count() or 1
+    desc = ""
+    budget = max(5.0, 120.0 / max(1, args.steps + args.warmup))
+    for s in range(args.warmup + args.steps):
+        v, cores, desc = cpu_oracle_sample(seconds_target=min(20.0, budget), rank_step=s % N_INPUTS)
+        if s >= args.warmup:
+            per_step.append(v)
+    value = statistics.mean(per_step)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": WORKLOAD.N / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; no dataset)",
+            "config": config_dict(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict():
+    w = WORKLOAD
+    return {"workload": f"realistic single MPC step: N={w.N} samples, J={w.J} joints, H={w.H}, "
+                        f"dt={w.dt}, {w.iters} iterations, rho={w.rho}, ADMM, row-normalised, FP32",
+            "N": w.N, "J": w.J, "H": w.H, "dt": w.dt, "iters": w.iters,
+            "l2": f"inputs larger than L2: {N_INPUTS} distinct step inputs cycled "
+                  f"({N_INPUTS * w.N * w.H * w.J * 4 / 1e6:.0f} MB)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1280)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=16)
+    ap.add_argument("--e2e-steps", type=int, default=32)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2608_25666_b300 import prism_proj as pp
+
+    ws, rank, local = dist_setup()
+    w = WORKLOAD
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # ---- inputs (seeded; per-rank independent batches) resident in HBM
+    xs, q0s, v0s = [], [], []
+    for s in range(N_INPUTS):
+        b = workloads.make_batch(w, step=rank * N_INPUTS + s)
+        xs.append(torch.from_numpy(b["xi"]).to(dev))
+        q0s.append(torch.from_numpy(b["q0"]).to(dev))
+        v0s.append(torch.from_numpy(b["v0"]).to(dev))
+    bounds = workloads.base_bounds(w.J)
+    outs = [torch.empty_like(xs[0]) for _ in range(N_INPUTS)]
+    prs = torch.empty((N_INPUTS, w.N, w.J), device=dev)
+    dus = torch.empty((N_INPUTS, w.N, w.J), device=dev)
+    P = pp.Projector(w.J, w.H, w.dt, bounds).factor(w.rho, pp.MODE_ADMM, pp.SCALE_ROWNORM)
+    q = P.query(w.N)
+    stream = torch.cuda.current_stream()
+
+    def step(s):
+        k = s % N_INPUTS
+        P.solve(q0s[k], v0s[k], xs[k], w.iters, out=outs[k], primal=prs[k], dual=dus[k], stream=stream)
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    # ---- timed region: K steps, events around each launch on the launching stream
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    ev[0].record(stream)
+    for s in range(K):
+        step(s)
+        ev[s + 1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier(ws)
+    clocks = sampler.stop()
+    per_step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(K)]
+    total_ms = ev[0].elapsed_time(ev[K])
+    total_ms = barrier_max(ws, total_ms)
+    value = ws * w.N * K / (total_ms / 1e3)
+    p50 = float(np.percentile(per_step_ms, 50))
+    p99 = float(np.percentile(per_step_ms, 99))
+
+    # ---- plain FP32 comparator on the same inputs
+    for s in range(3):
+        k = s % N_INPUTS
+        P.solve_plain(q0s[k], v0s[k], xs[k], w.iters, out=outs[k], primal=prs[k], dual=dus[k])
+    torch.cuda.synchronize()
+    pe = [torch.cuda.Event(enable_timing=True) for _ in range(args.plain_steps + 1)]
+    pe[0].record(stream)
+    for s in range(args.plain_steps):
+        k = s % N_INPUTS
+        P.solve_plain(q0s[k], v0s[k], xs[k], w.iters, out=outs[k], primal=prs[k], dual=dus[k])
+        pe[s + 1].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = [pe[s].elapsed_time(pe[s + 1]) for s in range(args.plain_steps)]
+    plain_value = w.N * args.plain_steps / (pe[0].elapsed_time(pe[-1]) / 1e3)
+
+    # ---- end to end through the host-buffer C-ABI call (pinned host memory)
+    hx = [torch.from_numpy(workloads.make_batch(w, step=rank * N_INPUTS + s)["xi"]).pin_memory()
+          for s in range(4)]
+    hq0 = torch.from_numpy(workloads.make_batch(w, step=0)["q0"]).pin_memory()
+    hv0 = torch.from_numpy(workloads.make_batch(w, step=0)["v0"]).pin_memory()
+    hout = torch.empty((w.N, w.H, w.J), dtype=torch.float32).pin_memory()
+    hpr = torch.empty((w.N, w.J), dtype=torch.float32).pin_memory()
+    hdu = torch.empty((w.N, w.J), dtype=torch.float32).pin_memory()
+    for s in range(3):
+        P.solve_host(hq0, hv0, hx[s % 4], w.iters, out=hout, primal=hpr, dual=hdu)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for s in range(args.e2e_steps):
+        P.solve_host(hq0, hv0, hx[s % 4], w.iters, out=hout, primal=hpr, dual=hdu)
+    e2e_s = barrier_max(ws, time.perf_counter() - t0)
+    e2e_value = ws * w.N * args.e2e_steps / e2e_s
+    h2d = (w.N * w.H * w.J + 2 * w.J) * 4
+    d2h = (w.N * w.H * w.J + 2 * w.N * w.J) * 4
+
+    # ---- roofline of the solve kernel (one launch per step)
+    avg_launch_s = statistics.mean(per_step_ms) / 1e3
+    flops = w.N * w.J * w.iters * flops_per_column_iteration(w.H)
+    achieved = flops / avg_launch_s / 1e12
+    peak = peak_fp32_tflops(q["num_sms"], 2032.0)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "solve_kernel (persistent ADMM, FP32 SIMT)",
+                "peak_basis": f"FP32 FMA issue rate {q['num_sms']} SMs x 128 lanes x 2 flop x 2032 MHz"
+                              " (max SM clock; derived, no measured FP32 peak)",
+                "algorithmic_flops_per_launch": flops,
+                "algorithmic_bytes_per_launch": 2 * w.N * w.H * w.J * 4 + 2 * w.N * w.J * 4}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, cores, desc = cpu_oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+                "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded white-noise samples; no dataset)",
+                "config": config_dict(),
+                "latency_ms": {"p50": p50, "p99": p99, "max": max(per_step_ms)},
+                "plain_gpu_admm": {"value": plain_value, "unit": UNIT, "steps": args.plain_steps,
+                                   "p50_ms": float(np.percentile(plain_ms, 50)),
+                                   "p99_ms": float(np.percentile(plain_ms, 99))},
+                "speedup_vs_plain": value / (ws * plain_value),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+                "gpu_launches": K,
+                "roofline": roofline,
+                "clocks": clocks,
+                "launch": q,
+                "wall_s_timed": t_wall}
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    P.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

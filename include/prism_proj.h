@@ -1,0 +1,192 @@
+/*
+ * prism_proj.h -- C ABI of libprism_proj, the batched QP projection of PRISM's
+ * sampling-based MPC on one NVIDIA B300 (sm_103a).
+ *
+ * The operation (paper: Sec. III-A, Eqs. proj_cost, proj_bounds, proj_boundary;
+ * Sec. III-D, Eqs. vel_bounds ... jerk_bounds, compact_qp, G_h_def, A_b_def):
+ * every sampled joint-velocity sequence xi (one column = one sample n and one
+ * joint j, an H-vector) is mapped to
+ *
+ *     argmin_x 1/2 ||x - xi||^2
+ *     s.t.  v_min <= x_k <= v_max                                  k = 1..H
+ *           q_min <= q0 + dt * sum_{i<=k} x_i <= q_max             k = 1..H
+ *           a_min <= (x_k - x_{k-1}) / dt <= a_max,  x_0 := v0      k = 1..H
+ *           j_min <= (x_k - 2 x_{k-1} + x_{k-2}) / dt^2 <= j_max    k = 2..H
+ *           x_1 = v0
+ *
+ * by a fixed number of iterations of the paper's three-step splitting
+ * (Eqs. admm_zeta, admm_primal, admm_KKT, admm_dual): a slack clip, a solve with
+ * a pre-factorised KKT matrix that depends only on (H, dt, rho) (Sec. III-D
+ * "Pre-computable factorization"), and a multiplier update.  The QP separates
+ * across joints (Sec. III-D "Joint-wise separability"), so a batch of N samples
+ * of J joints is N*J independent H-vector problems sharing one factorisation.
+ *
+ * Two iterations are offered (PRISM_MODE_*):
+ *   ADMM  (default) the three steps with the multiplier kept in constraint
+ *         space (one entry per two-sided bound row), so that the slack step sees
+ *         it.  Converges to the projection.  The printed iteration does not.
+ *   PAPER the iteration exactly as printed (primal-space multiplier lambda,
+ *         step factor rho/2 in Eq. admm_dual).  Kept for fidelity comparisons.
+ * Row scaling (PRISM_SCALE_*): ROWNORM divides each constraint row by its
+ * Euclidean norm (same feasible set; needed for FP32 accuracy), NONE uses the
+ * rows as printed.
+ *
+ * Conventions for every call:
+ *   - Every function returns a prism_status and never aborts; on failure
+ *     prism_last_error() returns a thread-local description.
+ *   - "device" pointers are CUDA device (or managed) memory of the device that
+ *     was current when the handle was created; that device must be current on
+ *     every call.  The caller owns every buffer it passes in.
+ *   - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Solves are
+ *     enqueued asynchronously; nothing in prism_proj_solve synchronises the
+ *     host.  Outputs are valid once the stream reaches the enqueued work.
+ *   - Layouts are the paper's stacking (Sec. III-D): time-major, joint-minor,
+ *     row-major [N][H][J] for sequences, [J] for per-joint values, [N][J] for
+ *     per-column values.
+ *   - Residuals: primal_res[n][j] = max(|x_1 - v0|, max over bound rows r of
+ *     max(0, c_r(x) - hi_r, lo_r - c_r(x)) / ||F_r||_2), the bound violation of
+ *     the returned x normalised by the row norm of the unscaled operator
+ *     (F = [I; dt L; D1/dt; D2/dt^2]); dual_res[n][j] = max_k |x^L_k - x^{L-1}_k|,
+ *     the size of the last primal step (0 when iters = 0).
+ *   - Initial iterate (the paper does not state one): x^0 = xi with x^0_1 := v0,
+ *     multiplier 0.
+ */
+#ifndef PRISM_PROJ_H
+#define PRISM_PROJ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct prism_proj_s *prism_proj_t;   /* opaque; created and owned by the library */
+
+typedef enum {
+    PRISM_OK = 0,
+    PRISM_ERR_INVALID_ARG = 1,      /* bad size, pointer, enum or bound ordering      */
+    PRISM_ERR_NOT_FACTORED = 2,     /* solve before prism_proj_factor                 */
+    PRISM_ERR_RHO_MISMATCH = 3,     /* solve's rho differs from the factored rho      */
+    PRISM_ERR_INFEASIBLE_BOUNDS = 4,/* bounds that admit no trajectory                */
+    PRISM_ERR_OOM = 5,              /* device or host allocation failed               */
+    PRISM_ERR_CUDA = 6,             /* a CUDA runtime call failed (text in last_error) */
+    PRISM_ERR_UNSUPPORTED = 7       /* valid request this build does not implement    */
+} prism_status;
+
+enum { PRISM_MODE_ADMM = 0, PRISM_MODE_PAPER = 1 };
+enum { PRISM_SCALE_ROWNORM = 0, PRISM_SCALE_NONE = 1 };
+enum { PRISM_PREC_FP32 = 0, PRISM_PREC_BF16X3 = 1, PRISM_PREC_TF32 = 2 };
+
+#define PRISM_MAX_H 132   /* horizon limit of the on-chip solve kernel          */
+#define PRISM_MAX_J 64    /* joints per sample handled by one thread block       */
+
+/*
+ * prism_proj_create -- a projector for J joints, horizon H, step dt.
+ *   Bounds are host arrays of length J (Eqs. vel_bounds, pos_bounds,
+ *   acc_bounds, jerk_bounds), copied at create: the caller may free them after
+ *   the call.  Requirements: 1 <= J <= PRISM_MAX_J, 2 <= H <= PRISM_MAX_H,
+ *   dt > 0 and finite, min <= max for every pair, and a_min <= 0 <= a_max (the
+ *   first acceleration row equals (x_1 - v0)/dt = 0 under the equality x_1 = v0,
+ *   so a bound excluding 0 makes the set empty: PRISM_ERR_INFEASIBLE_BOUNDS).
+ *   On success *out holds a new handle; on failure *out is set to NULL.
+ */
+prism_status prism_proj_create(int J, int H, double dt,
+                               const double *q_min, const double *q_max,
+                               const double *v_min, const double *v_max,
+                               const double *a_min, const double *a_max,
+                               const double *j_min, const double *j_max,
+                               prism_proj_t *out);
+
+/*
+ * prism_proj_factor -- the one-time per-shape factorisation (Sec. III-D
+ * "Pre-computable factorization"; KKT matrix M of Eq. admm_primal).
+ *   Builds B = I + c * rho * F^T W F in FP64 on the GPU (c = 1 for ADMM; c = 2
+ *   for PAPER, where G^T G = 2 F^T F), Cholesky-factors the block acting on
+ *   x_2..x_H, eliminates the equality x_1 = v0, and keeps K = [M^-1]_{1:H,1:H}
+ *   and kb = [M^-1]_{1:H,H+1} on the device (FP64, plus an FP32 copy used by
+ *   the solve).  rho > 0 is the paper's penalty delta.  prec must be
+ *   PRISM_PREC_FP32 in this build (others: PRISM_ERR_UNSUPPORTED).  Enqueued on
+ *   cuda_stream; re-factoring a handle replaces its factor (the caller orders
+ *   it after solves that still use the old one).
+ */
+prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, int prec,
+                               void *cuda_stream);
+
+/*
+ * prism_proj_solve -- project a batch (the hot path).
+ *   batch  N >= 0 samples (N = 0 is a no-op)
+ *   q0, v0 device float [J]: theta_init and thetadot_init (Eq. proj_boundary)
+ *   samples device float [N][H][J]
+ *   iters  >= 0 splitting iterations
+ *   rho    must equal the factored rho (else PRISM_ERR_RHO_MISMATCH): the
+ *          factorisation depends on it
+ *   out    device float [N][H][J]; may alias samples exactly (in place)
+ *   primal_res, dual_res device float [N][J], each may be NULL
+ *   One persistent launch: each thread block keeps a tile of columns on chip
+ *   for all iterations.  Boundary values outside the velocity bounds make the
+ *   problem infeasible; they are not detected at enqueue time (they live in
+ *   device memory) and show as primal_res >= their violation.
+ */
+prism_status prism_proj_solve(prism_proj_t h, int batch, const float *q0, const float *v0,
+                              const float *samples, int iters, double rho, float *out,
+                              float *primal_res, float *dual_res, void *cuda_stream);
+
+/*
+ * prism_proj_solve_plain -- the same projection computed by the plain FP32
+ * comparator: one thread per column, the iteration state in a device
+ * workspace that the handle allocates on first use (and grows), the cached
+ * inverse read from global memory.  Same arguments and results as
+ * prism_proj_solve up to FP32 rounding order.  Not for production use.
+ */
+prism_status prism_proj_solve_plain(prism_proj_t h, int batch, const float *q0, const float *v0,
+                                    const float *samples, int iters, double rho, float *out,
+                                    float *primal_res, float *dual_res, void *cuda_stream);
+
+/*
+ * prism_proj_solve_host -- end-to-end call on HOST buffers: copies q0, v0 and
+ * samples (host float arrays, layouts as above; pinned memory gives the
+ * fastest copies) to device staging buffers owned by the handle, runs
+ * prism_proj_solve, copies x (and the residuals when the pointers are not
+ * NULL) back to host memory, and synchronises cuda_stream before returning.
+ */
+prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_host,
+                                   const float *v0_host, const float *samples_host, int iters,
+                                   double rho, float *out_host, float *primal_res_host,
+                                   float *dual_res_host, void *cuda_stream);
+
+/*
+ * prism_proj_check_fp64 -- the final feasibility check in FP64 on the GPU:
+ * primal_res_fp64[n][j] (device double [N][J]) as defined above, evaluated in
+ * double precision from the FP32 trajectories x (device float [N][H][J]).
+ */
+prism_status prism_proj_check_fp64(prism_proj_t h, int batch, const float *q0, const float *v0,
+                                   const float *x, double *primal_res_fp64, void *cuda_stream);
+
+/*
+ * prism_proj_get_factor -- copy the FP64 factor to host memory (synchronous):
+ *   K_host [H][H] row-major = [M^-1]_{1:H,1:H}, kb_host [H] = [M^-1]_{1:H,H+1}.
+ */
+prism_status prism_proj_get_factor(prism_proj_t h, double *K_host, double *kb_host);
+
+/*
+ * prism_proj_query -- launch facts of the solve kernel for this handle:
+ *   out[0] columns per tile, out[1] samples per tile, out[2] thread blocks per
+ *   SM, out[3] persistent grid size for batch, out[4] dynamic shared memory
+ *   bytes per block, out[5] registers per thread, out[6] per-thread horizon
+ *   chunk (the kernel variant), out[7] number of SMs.
+ */
+prism_status prism_proj_query(prism_proj_t h, int batch, long long out[8]);
+
+/* prism_proj_destroy -- free the handle and its device memory (synchronises the device). */
+prism_status prism_proj_destroy(prism_proj_t h);
+
+/* Static text of a status code. */
+const char *prism_status_string(prism_status s);
+
+/* Thread-local text of the last failure in this thread ("" if none). */
+const char *prism_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRISM_PROJ_H */

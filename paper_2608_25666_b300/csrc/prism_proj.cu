@@ -1,0 +1,1175 @@
+// prism_proj.cu -- libprism_proj: the batched QP projection of PRISM's
+// sampling-based MPC (paper Sec. III-D) for one B300 (sm_103a).
+//
+// Kernels
+//   factor_kernel      one-time per-shape factorisation in FP64 (Sec. III-D
+//                      "Pre-computable factorization", KKT matrix of Eq. admm_primal)
+//   solve_kernel<HQ,M> the persistent solve: one thread block owns a tile of
+//                      columns (samples x joints) for all iterations, with the
+//                      iterate in shared memory and the multiplier in registers
+//   plain_kernel       the plain FP32 comparator: one thread per column, state in
+//                      a device workspace, no tiling
+//   check_kernel       FP64 feasibility check of returned trajectories
+//
+// Units used on the device.  Every constraint row r is kept in "integer stencil"
+// form Fh_r x in [lo_r, hi_r]: velocity x_i; position sum_{m<=i} x_m (the
+// printed row divided by dt); acceleration x_i - x_{i-1} (times dt);
+// jerk x_i - 2 x_{i-1} + x_{i-2} (times dt^2), with the x_0 (paper's
+// thetadot_0 = thetadot_init) terms moved into the bounds (Eqs. b_acc, b_jerk).
+// Positive row scaling changes neither the feasible set nor the splitting
+// once each row carries its own penalty rho*w_r: w_r = 1/||Fh_r||^2 reproduces
+// unit-norm rows (ROWNORM) and w_r = 1/d_r^2 the printed rows (NONE), d_r the
+// factor between the printed row and Fh_r.  Time index i is 0-based on the
+// device (paper index k = i + 1).
+//
+// Iteration in these units (ADMM mode; t = z - u):
+//   y = Fh x;  w = 2 y - t;  z = clip(w, lo, hi);  t <- z - y + t
+//   rhs = xi + rho * Fh^T (w_r * t);   x <- K rhs + kb v0
+// which is the slack clip, primal solve and multiplier update with u = y - t.
+// PAPER mode (Eqs. admm_zeta..admm_dual folded over the +/- row pairs, since
+// G^T (h - zeta) = F^T (y + clip(y)) and G^T G = 2 F^T F):
+//   y = Fh x;  p = y + clip(y);  g = Fh^T (w p);  rhs = rho g + lambda + xi;
+//   x <- K rhs + kb v0;  lambda <- lambda - (rho/2) Fh^T w (2 Fh x - p).
+#include "prism_proj.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <cstdint>
+#include <new>
+#include <string>
+
+namespace {
+
+thread_local std::string g_last_error;
+
+prism_status fail(prism_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? PRISM_ERR_OOM : PRISM_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+constexpr int CMAX = 64;         // columns per thread block
+constexpr int NTHREADS = 4 * CMAX;  // four threads per column (time quarters)
+
+// Bank-conflict-free column stride of the shared tiles: threads (c, b) of a warp
+// read row b*HQ + r, column c; rows of the four quarters must fall 8 banks apart.
+__host__ __device__ constexpr int col_stride(int hq) { return (hq & 1) ? 72 : 68; }
+
+enum : int { B_QMIN = 0, B_QMAX, B_VMIN, B_VMAX, B_AMIN, B_AMAX, B_JMIN, B_JMAX };
+
+// Per-row penalty weights (see header comment) for one horizon.
+struct Weights {
+    double wv, wa0, wa, wj0, wj;   // velocity, accel row 0 / others, jerk row 1 / others
+    bool rownorm;
+    double dt;
+    double wp(int i) const { return rownorm ? 1.0 / (i + 1) : dt * dt; }
+};
+
+Weights make_weights(int scale, double dt)
+{
+    Weights w;
+    w.dt = dt;
+    w.rownorm = scale == PRISM_SCALE_ROWNORM;
+    if (w.rownorm) {
+        w.wv = 1.0; w.wa0 = 1.0; w.wa = 0.5; w.wj0 = 0.2; w.wj = 1.0 / 6.0;
+    } else {
+        w.wv = 1.0; w.wa0 = w.wa = 1.0 / (dt * dt); w.wj0 = w.wj = 1.0 / (dt * dt * dt * dt);
+    }
+    return w;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct prism_proj_s {
+    int J = 0, H = 0;
+    double dt = 0.0;
+    int device = 0, num_sms = 0;
+    double *d_bounds = nullptr;          // [8][J] double
+    // factor
+    bool factored = false;
+    double rho = 0.0;
+    int mode = 0, scale = 0, prec = 0;
+    int n = 0, MP = 0;                   // reduced size H-1 and its padding to 4
+    double *d_K64 = nullptr;             // [n][n]  reduced K (rows/cols of x_2..x_H)
+    double *d_kb64 = nullptr;            // [n]
+    float *d_Kt32 = nullptr;             // [n][MP] transposed K, FP32, zero padded
+    float *d_kb32 = nullptr;             // [MP]
+    float *d_wp = nullptr;               // [PRISM_MAX_H] position-row weights
+    double *d_wfull = nullptr;           // factor input: per-row weights (4 blocks x H)
+    // plain comparator workspace
+    float *d_work = nullptr;
+    size_t work_elems = 0;
+    // host-buffer staging
+    float *d_stage = nullptr;
+    size_t stage_elems = 0;
+};
+
+namespace {
+
+// ===========================================================================
+// K1: FP64 factorisation (one thread block).
+//   B = I + rho_c * Fh^T W Fh  (H x H, shared memory), Cholesky of the block
+//   acting on x_2..x_H, then K' = B22^{-1}, kb' = -K' B21.
+// ===========================================================================
+__device__ __forceinline__ double d1c(int m, int i) { return (i == m ? 1.0 : 0.0) - (i == m - 1 ? 1.0 : 0.0); }
+__device__ __forceinline__ double d2c(int m, int i)
+{
+    return (i == m ? 1.0 : 0.0) - (i == m - 1 ? 2.0 : 0.0) + (i == m - 2 ? 1.0 : 0.0);
+}
+
+__global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wrow,
+                              double *__restrict__ K64, double *__restrict__ kb64,
+                              float *__restrict__ Kt32, float *__restrict__ kb32, int MP)
+{
+    extern __shared__ double Bs[];   // H*H
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const double *wv = wrow;          // [H] velocity rows
+    const double *wp = wrow + H;      // [H] position rows
+    const double *wa = wrow + 2 * H;  // [H] acceleration rows
+    const double *wj = wrow + 3 * H;  // [H] jerk rows by time (entry 0 unused)
+    for (int e = tid; e < H * H; e += nth) {
+        const int i = e / H, j = e % H;
+        double s = (i == j) ? wv[i] : 0.0;
+        for (int m = (i > j ? i : j); m < H; ++m) s += wp[m];
+        for (int m = 0; m < H; ++m) s += wa[m] * d1c(m, i) * d1c(m, j);
+        for (int m = 1; m < H; ++m) s += wj[m] * d2c(m, i) * d2c(m, j);
+        Bs[e] = (i == j ? 1.0 : 0.0) + rho_c * s;
+    }
+    __syncthreads();
+    const int n = H - 1;
+    // Cholesky of R = B[1:,1:] in place (lower triangle).
+    for (int k = 0; k < n; ++k) {
+        double *R = Bs + H + 1;   // R[i][j] = R[i*H + j]
+        if (tid == 0) R[k * H + k] = sqrt(R[k * H + k]);
+        __syncthreads();
+        const double d = R[k * H + k];
+        for (int i = k + 1 + tid; i < n; i += nth) R[i * H + k] /= d;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = tid; e < m * m; e += nth) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            if (j <= i) R[i * H + j] -= R[i * H + k] * R[j * H + k];
+        }
+        __syncthreads();
+    }
+    const double *R = Bs + H + 1;
+    // K' = R^{-1} = L^{-T} L^{-1}: thread c solves L y = e_c, L^T x = y in column c of K64.
+    for (int c = tid; c < n; c += nth) {
+        for (int i = 0; i < n; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            if (i >= c)
+                for (int m = c; m < i; ++m) s -= R[i * H + m] * K64[m * n + c];
+            K64[i * n + c] = (i >= c) ? s / R[i * H + i] : 0.0;
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = K64[i * n + c];
+            for (int m = i + 1; m < n; ++m) s -= R[m * H + i] * K64[m * n + c];
+            K64[i * n + c] = s / R[i * H + i];
+        }
+    }
+    __syncthreads();
+    // kb'[i] = -sum_j K'[i][j] B[j+1][0]
+    for (int i = tid; i < MP; i += nth) {
+        double s = 0.0;
+        if (i < n) {
+            for (int j = 0; j < n; ++j) s -= K64[i * n + j] * Bs[(j + 1) * H + 0];
+            kb64[i] = s;
+        }
+        kb32[i] = (float)s;
+    }
+    for (int e = tid; e < n * MP; e += nth) {
+        const int j = e / MP, i = e % MP;
+        Kt32[e] = (i < n) ? (float)K64[i * n + j] : 0.0f;
+    }
+}
+
+// ===========================================================================
+// Solve kernel parameters
+// ===========================================================================
+struct SolveParams {
+    int N, J, H, n, MP, iters, T, ntiles;
+    float rho;
+    double dt;
+    float wv, wa0, wa, wj0, wj;
+    const float *__restrict__ xi;
+    const float *__restrict__ q0;
+    const float *__restrict__ v0;
+    const double *__restrict__ bounds;   // [8][J]
+    const float *__restrict__ Kt;        // [n][MP]
+    const float *__restrict__ kb;        // [MP]
+    const float *__restrict__ wp;        // [>= H]
+    float *out;
+    float *primal;
+    float *dual;
+};
+
+// Two-sided bounds of one column in the device units (computed in double,
+// rounded once to float).
+struct ColBounds {
+    float vlo, vhi, plo, phi, alo, ahi, alo0, ahi0, jlo, jhi, jlo1, jhi1;
+};
+
+__device__ __forceinline__ ColBounds col_bounds(const double *__restrict__ bnd, int J, int j, double dt,
+                                                float q0f, float v0f)
+{
+    const double q0 = q0f, v0 = v0f;
+    ColBounds cb;
+    cb.vlo = (float)bnd[B_VMIN * J + j];
+    cb.vhi = (float)bnd[B_VMAX * J + j];
+    cb.plo = (float)((bnd[B_QMIN * J + j] - q0) / dt);
+    cb.phi = (float)((bnd[B_QMAX * J + j] - q0) / dt);
+    cb.alo = (float)(bnd[B_AMIN * J + j] * dt);
+    cb.ahi = (float)(bnd[B_AMAX * J + j] * dt);
+    cb.alo0 = (float)(bnd[B_AMIN * J + j] * dt + v0);
+    cb.ahi0 = (float)(bnd[B_AMAX * J + j] * dt + v0);
+    cb.jlo = (float)(bnd[B_JMIN * J + j] * dt * dt);
+    cb.jhi = (float)(bnd[B_JMAX * J + j] * dt * dt);
+    cb.jlo1 = (float)(bnd[B_JMIN * J + j] * dt * dt - v0);
+    cb.jhi1 = (float)(bnd[B_JMAX * J + j] * dt * dt - v0);
+    return cb;
+}
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+// 1/||Fh_r||_2 for the violation normalisation.
+__device__ __forceinline__ float inv_norm_pos(int i) { return rsqrtf((float)(i + 1)); }
+
+// Exclusive prefix / suffix sums over the four quarter-threads of a column.
+__device__ __forceinline__ float excl_prefix4(float v, int b)
+{
+    float s = v;
+    float t = __shfl_up_sync(0xffffffffu, s, 1, 4);
+    if (b >= 1) s += t;
+    t = __shfl_up_sync(0xffffffffu, s, 2, 4);
+    if (b >= 2) s += t;
+    return s - v;
+}
+__device__ __forceinline__ float excl_suffix4(float v, int b)
+{
+    float s = v;
+    float t = __shfl_down_sync(0xffffffffu, s, 1, 4);
+    if (b <= 2) s += t;
+    t = __shfl_down_sync(0xffffffffu, s, 2, 4);
+    if (b <= 1) s += t;
+    return s - v;
+}
+__device__ __forceinline__ float from_next4(float v, int b)
+{
+    const float t = __shfl_down_sync(0xffffffffu, v, 1, 4);
+    return b < 3 ? t : 0.0f;
+}
+
+// Weighted row values of one time quarter (four blocks).
+template <int HQ>
+struct Rows {
+    float v[HQ], p[HQ], a[HQ], j[HQ];
+};
+
+// The x window of a quarter: w[r] = x_{i0 + r - 2} (x_{-2} = x_{-1} = 0 for the
+// linear stencils), pre = sum of x over the earlier quarters.  The rows are
+// then y_v = w[r+2], y_p = pre + sum_{m<=r} w[m+2], y_a = w[r+2] - w[r+1],
+// y_j = y_a - (w[r+1] - w[r]).
+template <int HQ>
+struct XWin {
+    float w[HQ + 2];
+    float pre;
+};
+
+template <int HQ>
+__device__ __forceinline__ void load_xwin(const float *__restrict__ xs, int CP, int c, int b, XWin<HQ> &X)
+{
+    const int i0 = b * HQ;
+#pragma unroll
+    for (int r = 0; r < HQ + 2; ++r) X.w[r] = xs[(i0 + r) * CP + c];
+    float run = 0.0f;
+#pragma unroll
+    for (int r = 0; r < HQ; ++r) run += X.w[r + 2];
+    X.pre = excl_prefix4(run, b);
+}
+
+// g = Fh^T s for the quarter, given weighted row values s (zero on rows that
+// do not exist).  s.j[r] is the jerk row at time i0 + r.
+template <int HQ>
+__device__ __forceinline__ void apply_FT(const Rows<HQ> &s, int b, float g[HQ])
+{
+    float sps = 0.0f;
+#pragma unroll
+    for (int r = 0; r < HQ; ++r) sps += s.p[r];
+    float P = excl_suffix4(sps, b);
+    const float sa_n = from_next4(s.a[0], b);
+    const float sj_n0 = from_next4(s.j[0], b);
+    const float sj_n1 = from_next4(s.j[HQ > 1 ? 1 : 0], b);
+#pragma unroll
+    for (int r = HQ - 1; r >= 0; --r) {
+        P += s.p[r];
+        const float sa1 = (r + 1 < HQ) ? s.a[(r + 1) % HQ] : sa_n;
+        const float sj1 = (r + 1 < HQ) ? s.j[(r + 1) % HQ] : sj_n0;
+        const float sj2 = (r + 2 < HQ) ? s.j[(r + 2) % HQ] : ((r + 2 == HQ) ? sj_n0 : sj_n1);
+        g[r] = s.v[r] + P + (s.a[r] - sa1) + (s.j[r] - 2.0f * sj1 + sj2);
+    }
+}
+
+// GEMM phase: x[i+1] = sum_j K'[i][j] rhs[j+1] + kb[i] v0 for the tile,
+// 4x4 register micro-tiles.  Optionally records max |x_new - x_old| per column.
+__device__ __forceinline__ void kapply(float *__restrict__ xs, const float *__restrict__ rhs,
+                                       const float *__restrict__ Kts, const float *__restrict__ kbs,
+                                       const float *__restrict__ v0c, unsigned *__restrict__ dres,
+                                       int n, int MP, int CP, int ncolgroups, bool track)
+{
+    const int RG = (n + 3) >> 2;
+    const int ntile = RG * ncolgroups;
+    for (int tile = threadIdx.x; tile < ntile; tile += NTHREADS) {
+        const int rg = tile / ncolgroups, cg = tile - rg * ncolgroups;
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] = 0.0f;
+        const float4 *K4 = reinterpret_cast<const float4 *>(Kts) + rg;
+        const float4 *R4 = reinterpret_cast<const float4 *>(rhs + CP) + cg;   // rhs row j+1
+        const int kstride = MP >> 2, rstride = CP >> 2;
+#pragma unroll 4
+        for (int j = 0; j < n; ++j) {
+            const float4 kv = K4[j * kstride];
+            const float4 rv = R4[j * rstride];
+            const float kk[4] = {kv.x, kv.y, kv.z, kv.w};
+            const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(kk[a], rr[q], acc[a][q]);
+        }
+        const float4 vv = reinterpret_cast<const float4 *>(v0c)[cg];
+        const float vq[4] = {vv.x, vv.y, vv.z, vv.w};
+        float dmax[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = 4 * rg + a;
+            if (i < n) {
+                const float kbi = kbs[i];
+                float4 *dst = reinterpret_cast<float4 *>(xs + (i + 3) * CP) + cg;
+                float4 old = *dst;
+                float nv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) nv[q] = fmaf(kbi, vq[q], acc[a][q]);
+                if (track) {
+                    dmax[0] = fmaxf(dmax[0], fabsf(nv[0] - old.x));
+                    dmax[1] = fmaxf(dmax[1], fabsf(nv[1] - old.y));
+                    dmax[2] = fmaxf(dmax[2], fabsf(nv[2] - old.z));
+                    dmax[3] = fmaxf(dmax[3], fabsf(nv[3] - old.w));
+                }
+                *dst = make_float4(nv[0], nv[1], nv[2], nv[3]);
+            }
+        }
+        if (track) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) atomicMax(&dres[4 * cg + q], __float_as_uint(dmax[q]));
+        }
+    }
+}
+
+// ===========================================================================
+// K3: persistent solve.  HQ = horizon steps per thread (H <= 4*HQ), MODE =
+// PRISM_MODE_ADMM / PRISM_MODE_PAPER.
+// Shared memory (floats): xs[(4HQ+2) x CP] (rows: x_{-2}, x_{-1}, x_0 .. ),
+// rhs[4HQ x CP], Kt[n x MP], kb[MP], wp[4HQ], v0c[CMAX], dres[CMAX].
+// ===========================================================================
+template <int HQ>
+__host__ __device__ constexpr int solve_min_blocks() { return HQ <= 17 ? 2 : 1; }
+
+template <int HQ, int MODE>
+__global__ void __launch_bounds__(NTHREADS, solve_min_blocks<HQ>())
+solve_kernel(const SolveParams p)
+{
+    constexpr int HP = 4 * HQ;
+    constexpr int CP = col_stride(HQ);
+    extern __shared__ float4 smem4[];
+    float *xs = reinterpret_cast<float *>(smem4);
+    float *rhs = xs + (HP + 2) * CP;
+    float *Kts = rhs + HP * CP;
+    float *kbs = Kts + p.n * p.MP;
+    float *wps = kbs + p.MP;
+    float *v0c = wps + HP;
+    unsigned *dres = reinterpret_cast<unsigned *>(v0c + CMAX);
+
+    const int tid = threadIdx.x;
+    const int c = tid >> 2;       // column in tile
+    const int b = tid & 3;        // time quarter
+    const int i0 = b * HQ;
+    const int H = p.H, J = p.J, n = p.n;
+    const int HJ = H * J;
+    const float rho = p.rho;
+
+    // per-shape constants -> shared memory (once)
+    for (int e = tid; e < n * p.MP; e += NTHREADS) Kts[e] = p.Kt[e];
+    for (int e = tid; e < p.MP; e += NTHREADS) kbs[e] = p.kb[e];
+    for (int e = tid; e < HP; e += NTHREADS) wps[e] = (e < H) ? p.wp[e] : 0.0f;
+
+    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+        const int n0 = tile * p.T;
+        const int Tt = min(p.T, p.N - n0);
+        const int Ct = Tt * J;
+        const int ncg = (Ct + 3) >> 2;
+        __syncthreads();   // previous tile fully stored before xs is overwritten
+        // ---- a1: load the contiguous slab xi[n0 : n0+Tt][H][J] into xs rows 2..H+1
+        for (int e = tid; e < (HP + 2) * CP; e += NTHREADS) xs[e] = 0.0f;
+        if (tid < CMAX) {
+            const int j = tid % J;
+            v0c[tid] = (tid < Ct) ? p.v0[j] : 0.0f;
+            dres[tid] = 0u;
+        }
+        __syncthreads();
+        {
+            const float *src = p.xi + (size_t)n0 * HJ;
+            const int total = Tt * HJ;
+            for (int e = tid; e < total; e += NTHREADS) {
+                const int nl = e / HJ, rem = e - nl * HJ;
+                const int k = rem / J, j = rem - k * J;
+                xs[(k + 2) * CP + nl * J + j] = __ldg(src + e);
+            }
+        }
+        __syncthreads();
+        // ---- a2: per-column bounds in registers; xi quarter in registers; x_0 := v0
+        const bool colv = c < Ct;
+        const int jj = colv ? (c % J) : 0;
+        const float q0j = p.q0[jj], v0j = p.v0[jj];
+        const ColBounds cb = col_bounds(p.bounds, J, jj, p.dt, q0j, v0j);
+        float xi[HQ];
+#pragma unroll
+        for (int r = 0; r < HQ; ++r) xi[r] = xs[(i0 + r + 2) * CP + c];
+        __syncthreads();
+        if (b == 0) xs[2 * CP + c] = colv ? v0j : 0.0f;
+        __syncthreads();
+
+        // state
+        float t_v[HQ], t_p[HQ], t_a[HQ], t_j[HQ];   // ADMM: t = z - u per row
+        float lam[HQ];                              // PAPER: lambda (partially updated)
+        XWin<HQ> X;
+        load_xwin<HQ>(xs, CP, c, b, X);
+        {
+            float cs = X.pre;
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) {
+                const int i = i0 + r;
+                const bool vi = colv && i < H;
+                cs += X.w[r + 2];
+                const float ya = X.w[r + 2] - X.w[r + 1];
+                t_v[r] = vi ? X.w[r + 2] : 0.0f;
+                t_p[r] = vi ? cs : 0.0f;
+                t_a[r] = vi ? ya : 0.0f;
+                t_j[r] = (vi && i >= 1) ? ya - (X.w[r + 1] - X.w[r]) : 0.0f;
+                lam[r] = 0.0f;
+            }
+        }
+
+        for (int l = 0; l < p.iters; ++l) {
+            // ---- stencil phase: a3 slack / clip, a4 Fh^T, a6 multiplier, rhs
+            if (l > 0) load_xwin<HQ>(xs, CP, c, b, X);
+            Rows<HQ> s;
+            float g[HQ];
+            if (MODE == PRISM_MODE_ADMM) {
+                float cs = X.pre;
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    const bool vi = colv && i < H;
+                    cs += X.w[r + 2];
+                    const float yv = X.w[r + 2], yp = cs, ya = X.w[r + 2] - X.w[r + 1];
+                    const float yj = ya - (X.w[r + 1] - X.w[r]);
+                    float z;
+                    z = clampf(2.0f * yv - t_v[r], cb.vlo, cb.vhi);
+                    t_v[r] = vi ? (z - yv) + t_v[r] : 0.0f;
+                    s.v[r] = p.wv * t_v[r];
+                    z = clampf(2.0f * yp - t_p[r], cb.plo, cb.phi);
+                    t_p[r] = vi ? (z - yp) + t_p[r] : 0.0f;
+                    s.p[r] = wps[i] * t_p[r];
+                    z = (i == 0) ? clampf(2.0f * ya - t_a[r], cb.alo0, cb.ahi0)
+                                 : clampf(2.0f * ya - t_a[r], cb.alo, cb.ahi);
+                    t_a[r] = vi ? (z - ya) + t_a[r] : 0.0f;
+                    s.a[r] = ((i == 0) ? p.wa0 : p.wa) * t_a[r];
+                    z = (i == 1) ? clampf(2.0f * yj - t_j[r], cb.jlo1, cb.jhi1)
+                                 : clampf(2.0f * yj - t_j[r], cb.jlo, cb.jhi);
+                    t_j[r] = (vi && i >= 1) ? (z - yj) + t_j[r] : 0.0f;
+                    s.j[r] = ((i == 1) ? p.wj0 : p.wj) * t_j[r];
+                }
+                apply_FT<HQ>(s, b, g);
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    if (i >= 1 && i < H) rhs[i * CP + c] = fmaf(rho, g[r], xi[r]);
+                }
+            } else {
+                if (l > 0) {   // complete lambda <- lambda~ - rho Fh^T W y^l
+                    float cs = X.pre;
+#pragma unroll
+                    for (int r = 0; r < HQ; ++r) {
+                        const int i = i0 + r;
+                        const bool vi = colv && i < H;
+                        cs += X.w[r + 2];
+                        const float ya = X.w[r + 2] - X.w[r + 1];
+                        const float yj = ya - (X.w[r + 1] - X.w[r]);
+                        s.v[r] = vi ? p.wv * X.w[r + 2] : 0.0f;
+                        s.p[r] = vi ? wps[i] * cs : 0.0f;
+                        s.a[r] = vi ? ((i == 0) ? p.wa0 : p.wa) * ya : 0.0f;
+                        s.j[r] = (vi && i >= 1) ? ((i == 1) ? p.wj0 : p.wj) * yj : 0.0f;
+                    }
+                    apply_FT<HQ>(s, b, g);
+#pragma unroll
+                    for (int r = 0; r < HQ; ++r) lam[r] = fmaf(-rho, g[r], lam[r]);
+                }
+                float cs = X.pre;
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    const bool vi = colv && i < H;
+                    cs += X.w[r + 2];
+                    const float yv = X.w[r + 2], yp = cs, ya = X.w[r + 2] - X.w[r + 1];
+                    const float yj = ya - (X.w[r + 1] - X.w[r]);
+                    const float pv = yv + clampf(yv, cb.vlo, cb.vhi);
+                    const float pp = yp + clampf(yp, cb.plo, cb.phi);
+                    const float pa = ya + ((i == 0) ? clampf(ya, cb.alo0, cb.ahi0) : clampf(ya, cb.alo, cb.ahi));
+                    const float pj = yj + ((i == 1) ? clampf(yj, cb.jlo1, cb.jhi1) : clampf(yj, cb.jlo, cb.jhi));
+                    s.v[r] = vi ? p.wv * pv : 0.0f;
+                    s.p[r] = vi ? wps[i] * pp : 0.0f;
+                    s.a[r] = vi ? ((i == 0) ? p.wa0 : p.wa) * pa : 0.0f;
+                    s.j[r] = (vi && i >= 1) ? ((i == 1) ? p.wj0 : p.wj) * pj : 0.0f;
+                }
+                apply_FT<HQ>(s, b, g);
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    if (i >= 1 && i < H) rhs[i * CP + c] = fmaf(rho, g[r], lam[r] + xi[r]);
+                    lam[r] = fmaf(0.5f * rho, g[r], lam[r]);
+                }
+            }
+            __syncthreads();
+            // ---- a5: K-apply
+            kapply(xs, rhs, Kts, kbs, v0c, dres, n, p.MP, CP, ncg, l == p.iters - 1);
+            __syncthreads();
+        }
+
+        // ---- a7: residuals and store
+        load_xwin<HQ>(xs, CP, c, b, X);
+        float viol = 0.0f;
+        {
+            float cs = X.pre;
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) {
+                const int i = i0 + r;
+                cs += X.w[r + 2];
+                if (i < H) {
+                    const float yv = X.w[r + 2], yp = cs, ya = X.w[r + 2] - X.w[r + 1];
+                    const float yj = ya - (X.w[r + 1] - X.w[r]);
+                    viol = fmaxf(viol, fmaxf(yv - cb.vhi, cb.vlo - yv));
+                    viol = fmaxf(viol, fmaxf(yp - cb.phi, cb.plo - yp) * inv_norm_pos(i));
+                    const float ea = (i == 0) ? fmaxf(ya - cb.ahi0, cb.alo0 - ya)
+                                              : fmaxf(ya - cb.ahi, cb.alo - ya) * 0.70710678f;
+                    viol = fmaxf(viol, ea);
+                    if (i >= 1) {
+                        const float ej = (i == 1) ? fmaxf(yj - cb.jhi1, cb.jlo1 - yj) * 0.44721360f
+                                                  : fmaxf(yj - cb.jhi, cb.jlo - yj) * 0.40824829f;
+                        viol = fmaxf(viol, ej);
+                    }
+                }
+            }
+        }
+        viol = fmaxf(viol, __shfl_xor_sync(0xffffffffu, viol, 1, 4));
+        viol = fmaxf(viol, __shfl_xor_sync(0xffffffffu, viol, 2, 4));
+        if (b == 0 && colv) {
+            const size_t col = (size_t)n0 * J + c;
+            if (p.primal) p.primal[col] = viol;
+            if (p.dual) p.dual[col] = __uint_as_float(dres[c]);
+        }
+        {
+            float *dst = p.out + (size_t)n0 * HJ;
+            const int total = Tt * HJ;
+            for (int e = tid; e < total; e += NTHREADS) {
+                const int nl = e / HJ, rem = e - nl * HJ;
+                const int k = rem / J, j = rem - k * J;
+                dst[e] = xs[(k + 2) * CP + nl * J + j];
+            }
+        }
+    }
+}
+
+// ===========================================================================
+// K2: plain FP32 comparator.  One thread per column; the iterate, the
+// multiplier rows and the right-hand side live in a workspace laid out
+// [row][column] (coalesced across threads); K is read through the L1 cache.
+// ===========================================================================
+template <int MODE>
+__global__ void __launch_bounds__(128) plain_kernel(const SolveParams p, float *__restrict__ work, long long ncols)
+{
+    const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    const int H = p.H, J = p.J, n = p.n;
+    const long long nn = col / J;
+    const int j = (int)(col % J);
+    const float rho = p.rho;
+    float *x = work + col;                  // H rows
+    float *tv = x + (size_t)H * ncols;      // 4 H rows of multiplier state
+    float *tp = tv + (size_t)H * ncols;
+    float *ta = tp + (size_t)H * ncols;
+    float *tj = ta + (size_t)H * ncols;
+    float *rh = tj + (size_t)H * ncols;     // H rows right-hand side
+#define AT(ptr, i) ptr[(size_t)(i) * ncols]
+    const float q0j = p.q0[j], v0j = p.v0[j];
+    const ColBounds cb = col_bounds(p.bounds, J, j, p.dt, q0j, v0j);
+    const float *xi = p.xi + (size_t)nn * H * J + j;
+    for (int i = 0; i < H; ++i) AT(x, i) = (i == 0) ? v0j : xi[(size_t)i * J];
+    // y = Fh x helpers in the loop
+    auto yv = [&](int i) { return AT(x, i); };
+    auto ya = [&](int i) { return AT(x, i) - (i >= 1 ? AT(x, i - 1) : 0.0f); };
+    auto yj = [&](int i) {
+        const float xm1 = i >= 1 ? AT(x, i - 1) : 0.0f, xm2 = i >= 2 ? AT(x, i - 2) : 0.0f;
+        return (AT(x, i) - xm1) - (xm1 - xm2);
+    };
+    {
+        float cs = 0.0f;
+        for (int i = 0; i < H; ++i) {
+            cs += AT(x, i);
+            if (MODE == PRISM_MODE_ADMM) {
+                AT(tv, i) = yv(i);
+                AT(tp, i) = cs;
+                AT(ta, i) = ya(i);
+                AT(tj, i) = i >= 1 ? yj(i) : 0.0f;
+            } else {
+                AT(tv, i) = 0.0f;   // lambda lives in tv for PAPER mode
+            }
+        }
+    }
+    float dmax = 0.0f;
+    for (int l = 0; l < p.iters; ++l) {
+        // s = weights * (t  or  p) per row, stored back into the row arrays
+        float cs = 0.0f;
+        for (int i = 0; i < H; ++i) {
+            cs += AT(x, i);
+            const float y_v = yv(i), y_p = cs, y_a = ya(i), y_j = i >= 1 ? yj(i) : 0.0f;
+            const float alo = i == 0 ? cb.alo0 : cb.alo, ahi = i == 0 ? cb.ahi0 : cb.ahi;
+            const float jlo = i == 1 ? cb.jlo1 : cb.jlo, jhi = i == 1 ? cb.jhi1 : cb.jhi;
+            const float wa = i == 0 ? p.wa0 : p.wa, wj = i == 1 ? p.wj0 : p.wj;
+            if (MODE == PRISM_MODE_ADMM) {
+                float t;
+                t = AT(tv, i); t = (clampf(2.f * y_v - t, cb.vlo, cb.vhi) - y_v) + t; AT(tv, i) = t;
+                t = AT(tp, i); t = (clampf(2.f * y_p - t, cb.plo, cb.phi) - y_p) + t; AT(tp, i) = t;
+                t = AT(ta, i); t = (clampf(2.f * y_a - t, alo, ahi) - y_a) + t; AT(ta, i) = t;
+                if (i >= 1) { t = AT(tj, i); t = (clampf(2.f * y_j - t, jlo, jhi) - y_j) + t; AT(tj, i) = t; }
+            } else {
+                // tp/ta/tj hold w*(y + clip(y)); rh temporarily holds w*y per block sum
+                AT(tp, i) = p.wp[i] * (y_p + clampf(y_p, cb.plo, cb.phi));
+                AT(ta, i) = wa * (y_a + clampf(y_a, alo, ahi));
+                AT(tj, i) = i >= 1 ? wj * (y_j + clampf(y_j, jlo, jhi)) : 0.0f;
+                AT(rh, i) = p.wv * (y_v + clampf(y_v, cb.vlo, cb.vhi));
+            }
+        }
+        if (MODE == PRISM_MODE_ADMM) {
+            // rhs_i = xi_i + rho * (Fh^T W t)_i
+            float P = 0.0f;
+            for (int i = H - 1; i >= 0; --i) {
+                P += p.wp[i] * AT(tp, i);
+                const float sa0 = (i == 0 ? p.wa0 : p.wa) * AT(ta, i);
+                const float sa1 = (i + 1 < H) ? p.wa * AT(ta, i + 1) : 0.0f;
+                auto sj = [&](int m) { return (m >= 1 && m < H) ? ((m == 1 ? p.wj0 : p.wj) * AT(tj, m)) : 0.0f; };
+                const float g = p.wv * AT(tv, i) + P + (sa0 - sa1) + (sj(i) - 2.f * sj(i + 1) + sj(i + 2));
+                AT(rh, i) = (i == 0) ? 0.0f : fmaf(rho, g, xi[(size_t)i * J]);
+            }
+        } else {
+            // lambda update needs Fh^T W y of the current x (l > 0), then g = Fh^T W p
+            float P = 0.0f, Py = 0.0f;
+            // compute gy (Fh^T W y) and g (Fh^T W p) together, write rhs and lambda
+            // using the rows stored above (p values) and recomputed y values.
+            float cs2 = 0.0f;
+            for (int i = 0; i < H; ++i) cs2 += AT(x, i);
+            for (int i = H - 1; i >= 0; --i) {
+                const float y_pi = cs2;
+                cs2 -= AT(x, i);
+                P += AT(tp, i);
+                Py += p.wp[i] * y_pi;
+                const float wa_i = (i == 0 ? p.wa0 : p.wa);
+                const float sa0 = AT(ta, i), sa1 = (i + 1 < H) ? AT(ta, i + 1) : 0.0f;
+                const float ya0 = wa_i * ya(i), ya1 = (i + 1 < H) ? p.wa * ya(i + 1) : 0.0f;
+                auto sj = [&](int m) { return (m >= 1 && m < H) ? AT(tj, m) : 0.0f; };
+                auto syj = [&](int m) { return (m >= 1 && m < H) ? (m == 1 ? p.wj0 : p.wj) * yj(m) : 0.0f; };
+                const float g = AT(rh, i) + P + (sa0 - sa1) + (sj(i) - 2.f * sj(i + 1) + sj(i + 2));
+                const float gy = p.wv * yv(i) + Py + (ya0 - ya1) + (syj(i) - 2.f * syj(i + 1) + syj(i + 2));
+                float lam = AT(tv, i);
+                if (l > 0) lam = fmaf(-rho, gy, lam);
+                AT(rh, i) = (i == 0) ? 0.0f : fmaf(rho, g, lam + xi[(size_t)i * J]);
+                AT(tv, i) = fmaf(0.5f * rho, g, lam);
+            }
+        }
+        // x <- K rhs + kb v0
+        const bool last = (l == p.iters - 1);
+        for (int i = 0; i < n; ++i) {
+            float acc = 0.0f;
+            const float *Kcol = p.Kt + i;   // Kt[jj][i]
+            for (int jj = 0; jj < n; ++jj) acc = fmaf(__ldg(Kcol + (size_t)jj * p.MP), AT(rh, jj + 1), acc);
+            const float nv = fmaf(__ldg(p.kb + i), v0j, acc);
+            if (last) dmax = fmaxf(dmax, fabsf(nv - AT(x, i + 1)));
+            // rhs rows are read for all i before x is overwritten? x is not read by the K-apply.
+            AT(x, i + 1) = nv;
+        }
+    }
+    // residual
+    float viol = 0.0f, cs = 0.0f;
+    for (int i = 0; i < H; ++i) {
+        cs += AT(x, i);
+        const float y_v = yv(i), y_a = ya(i);
+        viol = fmaxf(viol, fmaxf(y_v - cb.vhi, cb.vlo - y_v));
+        viol = fmaxf(viol, fmaxf(cs - cb.phi, cb.plo - cs) * rsqrtf((float)(i + 1)));
+        viol = fmaxf(viol, i == 0 ? fmaxf(y_a - cb.ahi0, cb.alo0 - y_a)
+                                  : fmaxf(y_a - cb.ahi, cb.alo - y_a) * 0.70710678f);
+        if (i >= 1) {
+            const float y_j = yj(i);
+            viol = fmaxf(viol, i == 1 ? fmaxf(y_j - cb.jhi1, cb.jlo1 - y_j) * 0.44721360f
+                                      : fmaxf(y_j - cb.jhi, cb.jlo - y_j) * 0.40824829f);
+        }
+    }
+    float *out = p.out + (size_t)nn * H * J + j;
+    for (int i = 0; i < H; ++i) out[(size_t)i * J] = AT(x, i);
+    if (p.primal) p.primal[col] = viol;
+    if (p.dual) p.dual[col] = dmax;
+#undef AT
+}
+
+// ===========================================================================
+// K5: FP64 feasibility check, written from the derivative definitions.
+// ===========================================================================
+__global__ void check_kernel(int N, int J, int H, double dt, const double *__restrict__ bnd,
+                             const float *__restrict__ q0, const float *__restrict__ v0,
+                             const float *__restrict__ x, double *__restrict__ res)
+{
+    const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= (long long)N * J) return;
+    const long long nn = col / J;
+    const int j = (int)(col % J);
+    const double qmin = bnd[B_QMIN * J + j], qmax = bnd[B_QMAX * J + j];
+    const double vmin = bnd[B_VMIN * J + j], vmax = bnd[B_VMAX * J + j];
+    const double amin = bnd[B_AMIN * J + j], amax = bnd[B_AMAX * J + j];
+    const double jmin = bnd[B_JMIN * J + j], jmax = bnd[B_JMAX * J + j];
+    const double q = q0[j], v = v0[j];
+    const float *xc = x + (size_t)nn * H * J + j;
+    double viol = fabs((double)xc[0] - v);
+    double pos = q, prevv = v, preva = 0.0;
+    const double s2 = sqrt(2.0), s5 = sqrt(5.0), s6 = sqrt(6.0);
+    for (int k = 0; k < H; ++k) {
+        const double xk = xc[(size_t)k * J];
+        pos += dt * xk;
+        const double acc = (xk - prevv) / dt;
+        viol = fmax(viol, fmax(xk - vmax, vmin - xk));
+        viol = fmax(viol, fmax(pos - qmax, qmin - pos) / (dt * sqrt((double)(k + 1))));
+        viol = fmax(viol, fmax(acc - amax, amin - acc) / ((k == 0 ? 1.0 : s2) / dt));
+        if (k >= 1) {
+            const double jerk = (acc - preva) / dt;
+            viol = fmax(viol, fmax(jerk - jmax, jmin - jerk) / ((k == 1 ? s5 : s6) / (dt * dt)));
+        }
+        prevv = xk;
+        preva = acc;
+    }
+    res[col] = viol;
+}
+
+// ===========================================================================
+// Host side
+// ===========================================================================
+typedef void (*solve_fn)(const SolveParams);
+
+struct Variant {
+    int hq;
+    solve_fn admm, paper;
+};
+
+#define VARIANT(HQv) {HQv, solve_kernel<HQv, PRISM_MODE_ADMM>, solve_kernel<HQv, PRISM_MODE_PAPER>}
+const Variant kVariants[] = {VARIANT(3), VARIANT(5), VARIANT(7), VARIANT(9), VARIANT(11),
+                             VARIANT(13), VARIANT(15), VARIANT(17), VARIANT(21), VARIANT(25),
+                             VARIANT(29), VARIANT(33)};
+#undef VARIANT
+
+const Variant *pick_variant(int H)
+{
+    for (const Variant &v : kVariants)
+        if (4 * v.hq >= H) return &v;
+    return nullptr;
+}
+
+size_t solve_smem_bytes(int hq, int n, int MP)
+{
+    const int HP = 4 * hq, CP = col_stride(hq);
+    const size_t floats = (size_t)(HP + 2) * CP + (size_t)HP * CP + (size_t)n * MP + MP + HP + CMAX + CMAX;
+    return floats * sizeof(float);
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+prism_status check_handle(prism_proj_t h)
+{
+    if (!h) return fail(PRISM_ERR_INVALID_ARG, "null handle");
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != h->device)
+        return fail(PRISM_ERR_INVALID_ARG, "current device %d differs from the handle's device %d", dev, h->device);
+    return PRISM_OK;
+}
+
+prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const float *v0,
+                           const float *samples, int iters, double rho, float *out, SolveParams &p)
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    if (!h->factored) return fail(PRISM_ERR_NOT_FACTORED, "prism_proj_factor has not been called");
+    if (batch < 0) return fail(PRISM_ERR_INVALID_ARG, "batch < 0");
+    if (iters < 0) return fail(PRISM_ERR_INVALID_ARG, "iters < 0");
+    if (!(rho > 0.0) || !is_finite(rho)) return fail(PRISM_ERR_INVALID_ARG, "rho must be positive and finite");
+    if (std::fabs(rho - h->rho) > 1e-12 * std::fabs(h->rho))
+        return fail(PRISM_ERR_RHO_MISMATCH, "rho %.17g differs from the factored rho %.17g", rho, h->rho);
+    if (batch > 0 && (!q0 || !v0 || !samples || !out))
+        return fail(PRISM_ERR_INVALID_ARG, "null device pointer");
+    if ((long long)batch * h->H * h->J > (long long)INT32_MAX)
+        return fail(PRISM_ERR_INVALID_ARG, "batch*H*J exceeds 2^31-1");
+    const Weights w = make_weights(h->scale, h->dt);
+    p.N = batch; p.J = h->J; p.H = h->H; p.n = h->n; p.MP = h->MP; p.iters = iters;
+    p.T = std::max(1, CMAX / h->J);
+    p.ntiles = (batch + p.T - 1) / p.T;
+    p.rho = (float)rho;
+    p.dt = h->dt;
+    p.wv = (float)w.wv; p.wa0 = (float)w.wa0; p.wa = (float)w.wa; p.wj0 = (float)w.wj0; p.wj = (float)w.wj;
+    p.xi = samples; p.q0 = q0; p.v0 = v0; p.bounds = h->d_bounds;
+    p.Kt = h->d_Kt32; p.kb = h->d_kb32; p.wp = h->d_wp;
+    p.out = out; p.primal = nullptr; p.dual = nullptr;
+    return PRISM_OK;
+}
+
+prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t &smem, int &blocks_per_sm,
+                           int &grid, solve_fn &fn)
+{
+    v = pick_variant(h->H);
+    if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", h->H);
+    fn = (h->mode == PRISM_MODE_ADMM) ? v->admm : v->paper;
+    smem = solve_smem_bytes(v->hq, h->n, h->MP);
+    CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, (const void *)fn, NTHREADS, smem));
+    if (blocks_per_sm < 1) return fail(PRISM_ERR_UNSUPPORTED, "solve kernel does not fit on an SM (smem %zu)", smem);
+    const int T = std::max(1, CMAX / h->J);
+    const int ntiles = (batch + T - 1) / T;
+    grid = std::min(ntiles, blocks_per_sm * h->num_sms);
+    return PRISM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *prism_status_string(prism_status s)
+{
+    switch (s) {
+    case PRISM_OK: return "PRISM_OK";
+    case PRISM_ERR_INVALID_ARG: return "PRISM_ERR_INVALID_ARG";
+    case PRISM_ERR_NOT_FACTORED: return "PRISM_ERR_NOT_FACTORED";
+    case PRISM_ERR_RHO_MISMATCH: return "PRISM_ERR_RHO_MISMATCH";
+    case PRISM_ERR_INFEASIBLE_BOUNDS: return "PRISM_ERR_INFEASIBLE_BOUNDS";
+    case PRISM_ERR_OOM: return "PRISM_ERR_OOM";
+    case PRISM_ERR_CUDA: return "PRISM_ERR_CUDA";
+    case PRISM_ERR_UNSUPPORTED: return "PRISM_ERR_UNSUPPORTED";
+    }
+    return "PRISM_ERR_UNKNOWN";
+}
+
+const char *prism_last_error(void) { return g_last_error.c_str(); }
+
+prism_status prism_proj_create(int J, int H, double dt, const double *q_min, const double *q_max,
+                               const double *v_min, const double *v_max, const double *a_min,
+                               const double *a_max, const double *j_min, const double *j_max,
+                               prism_proj_t *out)
+{
+    if (!out) return fail(PRISM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (J < 1 || J > PRISM_MAX_J) return fail(PRISM_ERR_INVALID_ARG, "J=%d outside [1, %d]", J, PRISM_MAX_J);
+    if (H < 2 || H > PRISM_MAX_H) return fail(PRISM_ERR_INVALID_ARG, "H=%d outside [2, %d]", H, PRISM_MAX_H);
+    if (!(dt > 0.0) || !is_finite(dt)) return fail(PRISM_ERR_INVALID_ARG, "dt must be positive and finite");
+    const double *arrs[8] = {q_min, q_max, v_min, v_max, a_min, a_max, j_min, j_max};
+    for (int b = 0; b < 8; ++b)
+        if (!arrs[b]) return fail(PRISM_ERR_INVALID_ARG, "bound array %d is NULL", b);
+    for (int j = 0; j < J; ++j) {
+        for (int b = 0; b < 8; ++b)
+            if (!is_finite(arrs[b][j])) return fail(PRISM_ERR_INVALID_ARG, "bound %d of joint %d is not finite", b, j);
+        for (int b = 0; b < 8; b += 2)
+            if (arrs[b][j] > arrs[b + 1][j])
+                return fail(PRISM_ERR_INVALID_ARG, "joint %d: lower bound %d exceeds upper bound", j, b / 2);
+        if (a_min[j] > 0.0 || a_max[j] < 0.0)
+            return fail(PRISM_ERR_INFEASIBLE_BOUNDS,
+                        "joint %d: acceleration bounds must contain 0 (first row is 0 under x_1 = v0)", j);
+    }
+    prism_proj_t h = new (std::nothrow) prism_proj_s;
+    if (!h) return fail(PRISM_ERR_OOM, "host allocation failed");
+    h->J = J; h->H = H; h->dt = dt;
+    h->n = H - 1;
+    h->MP = (h->n + 3) & ~3;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    double hb[8 * PRISM_MAX_J];
+    for (int b = 0; b < 8; ++b)
+        for (int j = 0; j < J; ++j) hb[b * J + j] = arrs[b][j];
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_bounds, sizeof(double) * 8 * J);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_bounds, hb, sizeof(double) * 8 * J, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        prism_status st = fail(e == cudaErrorMemoryAllocation ? PRISM_ERR_OOM : PRISM_ERR_CUDA, "create: %s",
+                               cudaGetErrorString(e));
+        cudaFree(h->d_bounds);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return PRISM_OK;
+}
+
+prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, int prec, void *cuda_stream)
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    if (!(rho > 0.0) || !is_finite(rho)) return fail(PRISM_ERR_INVALID_ARG, "rho must be positive and finite");
+    if (mode != PRISM_MODE_ADMM && mode != PRISM_MODE_PAPER) return fail(PRISM_ERR_INVALID_ARG, "bad mode %d", mode);
+    if (scale != PRISM_SCALE_ROWNORM && scale != PRISM_SCALE_NONE) return fail(PRISM_ERR_INVALID_ARG, "bad scale %d", scale);
+    if (prec != PRISM_PREC_FP32 && prec != PRISM_PREC_BF16X3 && prec != PRISM_PREC_TF32)
+        return fail(PRISM_ERR_INVALID_ARG, "bad precision %d", prec);
+    if (prec != PRISM_PREC_FP32) return fail(PRISM_ERR_UNSUPPORTED, "only PRISM_PREC_FP32 is built");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int H = h->H, n = h->n, MP = h->MP;
+    if (!h->d_K64) {
+        CUDA_TRY(cudaMalloc(&h->d_K64, sizeof(double) * n * n));
+        CUDA_TRY(cudaMalloc(&h->d_kb64, sizeof(double) * std::max(n, 1)));
+        CUDA_TRY(cudaMalloc(&h->d_Kt32, sizeof(float) * std::max(n * MP, 4)));
+        CUDA_TRY(cudaMalloc(&h->d_kb32, sizeof(float) * std::max(MP, 4)));
+        CUDA_TRY(cudaMalloc(&h->d_wp, sizeof(float) * PRISM_MAX_H));
+        CUDA_TRY(cudaMalloc(&h->d_wfull, sizeof(double) * 4 * H));
+    }
+    const Weights w = make_weights(scale, h->dt);
+    double wfull[4 * PRISM_MAX_H];
+    float wp32[PRISM_MAX_H];
+    for (int i = 0; i < H; ++i) {
+        wfull[i] = w.wv;
+        wfull[H + i] = w.wp(i);
+        wfull[2 * H + i] = (i == 0) ? w.wa0 : w.wa;
+        wfull[3 * H + i] = (i == 0) ? 0.0 : ((i == 1) ? w.wj0 : w.wj);
+    }
+    for (int i = 0; i < PRISM_MAX_H; ++i) wp32[i] = (i < H) ? (float)w.wp(i) : 0.0f;
+    // synchronous host->device copies of small tables (pageable source)
+    CUDA_TRY(cudaMemcpyAsync(h->d_wfull, wfull, sizeof(double) * 4 * H, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(h->d_wp, wp32, sizeof(float) * PRISM_MAX_H, cudaMemcpyHostToDevice, s));
+    const size_t smem = sizeof(double) * H * H;
+    CUDA_TRY(cudaFuncSetAttribute((const void *)factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const double rho_c = (mode == PRISM_MODE_PAPER ? 2.0 : 1.0) * rho;
+    factor_kernel<<<1, 256, smem, s>>>(H, rho_c, h->d_wfull, h->d_K64, h->d_kb64, h->d_Kt32, h->d_kb32, MP);
+    CUDA_TRY(cudaGetLastError());
+    // the host tables above are stack memory: make sure the copies completed
+    CUDA_TRY(cudaStreamSynchronize(s));
+    h->factored = true;
+    h->rho = rho;
+    h->mode = mode;
+    h->scale = scale;
+    h->prec = prec;
+    return PRISM_OK;
+}
+
+prism_status prism_proj_solve(prism_proj_t h, int batch, const float *q0, const float *v0, const float *samples,
+                              int iters, double rho, float *out, float *primal_res, float *dual_res,
+                              void *cuda_stream)
+{
+    SolveParams p;
+    prism_status st = prepare_solve(h, batch, q0, v0, samples, iters, rho, out, p);
+    if (st) return st;
+    if (batch == 0) return PRISM_OK;
+    p.primal = primal_res;
+    p.dual = dual_res;
+    const Variant *v;
+    size_t smem;
+    int bps, grid;
+    solve_fn fn;
+    st = launch_config(h, batch, v, smem, bps, grid, fn);
+    if (st) return st;
+    fn<<<grid, NTHREADS, smem, (cudaStream_t)cuda_stream>>>(p);
+    CUDA_TRY(cudaGetLastError());
+    return PRISM_OK;
+}
+
+prism_status prism_proj_solve_plain(prism_proj_t h, int batch, const float *q0, const float *v0,
+                                    const float *samples, int iters, double rho, float *out, float *primal_res,
+                                    float *dual_res, void *cuda_stream)
+{
+    SolveParams p;
+    prism_status st = prepare_solve(h, batch, q0, v0, samples, iters, rho, out, p);
+    if (st) return st;
+    if (batch == 0) return PRISM_OK;
+    p.primal = primal_res;
+    p.dual = dual_res;
+    const long long ncols = (long long)batch * h->J;
+    const size_t need = (size_t)ncols * 6 * h->H;
+    if (need > h->work_elems) {
+        if (h->d_work) {
+            CUDA_TRY(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+            CUDA_TRY(cudaFree(h->d_work));
+            h->d_work = nullptr;
+            h->work_elems = 0;
+        }
+        CUDA_TRY(cudaMalloc(&h->d_work, need * sizeof(float)));
+        h->work_elems = need;
+    }
+    const int tpb = 128;
+    const long long blocks = (ncols + tpb - 1) / tpb;
+    if (h->mode == PRISM_MODE_ADMM)
+        plain_kernel<PRISM_MODE_ADMM><<<(unsigned)blocks, tpb, 0, (cudaStream_t)cuda_stream>>>(p, h->d_work, ncols);
+    else
+        plain_kernel<PRISM_MODE_PAPER><<<(unsigned)blocks, tpb, 0, (cudaStream_t)cuda_stream>>>(p, h->d_work, ncols);
+    CUDA_TRY(cudaGetLastError());
+    return PRISM_OK;
+}
+
+prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_host, const float *v0_host,
+                                   const float *samples_host, int iters, double rho, float *out_host,
+                                   float *primal_res_host, float *dual_res_host, void *cuda_stream)
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    if (batch < 0) return fail(PRISM_ERR_INVALID_ARG, "batch < 0");
+    if (batch == 0) return PRISM_OK;
+    if (!q0_host || !v0_host || !samples_host || !out_host) return fail(PRISM_ERR_INVALID_ARG, "null host pointer");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t seq = (size_t)batch * h->H * h->J, cols = (size_t)batch * h->J;
+    const size_t need = seq + 2 * cols + 2 * (size_t)h->J + 8;
+    if (need > h->stage_elems) {
+        if (h->d_stage) {
+            CUDA_TRY(cudaStreamSynchronize(s));
+            CUDA_TRY(cudaFree(h->d_stage));
+            h->d_stage = nullptr;
+            h->stage_elems = 0;
+        }
+        CUDA_TRY(cudaMalloc(&h->d_stage, need * sizeof(float)));
+        h->stage_elems = need;
+    }
+    float *d_x = h->d_stage;                 // samples in, trajectories out (in place)
+    float *d_pr = d_x + seq;
+    float *d_du = d_pr + cols;
+    float *d_q0 = d_du + cols;
+    float *d_v0 = d_q0 + h->J;
+    CUDA_TRY(cudaMemcpyAsync(d_q0, q0_host, sizeof(float) * h->J, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_v0, v0_host, sizeof(float) * h->J, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_x, samples_host, sizeof(float) * seq, cudaMemcpyHostToDevice, s));
+    st = prism_proj_solve(h, batch, d_q0, d_v0, d_x, iters, rho, d_x, primal_res_host ? d_pr : nullptr,
+                          dual_res_host ? d_du : nullptr, cuda_stream);
+    if (st) return st;
+    CUDA_TRY(cudaMemcpyAsync(out_host, d_x, sizeof(float) * seq, cudaMemcpyDeviceToHost, s));
+    if (primal_res_host) CUDA_TRY(cudaMemcpyAsync(primal_res_host, d_pr, sizeof(float) * cols, cudaMemcpyDeviceToHost, s));
+    if (dual_res_host) CUDA_TRY(cudaMemcpyAsync(dual_res_host, d_du, sizeof(float) * cols, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return PRISM_OK;
+}
+
+prism_status prism_proj_check_fp64(prism_proj_t h, int batch, const float *q0, const float *v0, const float *x,
+                                   double *primal_res_fp64, void *cuda_stream)
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    if (batch < 0) return fail(PRISM_ERR_INVALID_ARG, "batch < 0");
+    if (batch == 0) return PRISM_OK;
+    if (!q0 || !v0 || !x || !primal_res_fp64) return fail(PRISM_ERR_INVALID_ARG, "null device pointer");
+    const long long ncols = (long long)batch * h->J;
+    const int tpb = 128;
+    check_kernel<<<(unsigned)((ncols + tpb - 1) / tpb), tpb, 0, (cudaStream_t)cuda_stream>>>(
+        batch, h->J, h->H, h->dt, h->d_bounds, q0, v0, x, primal_res_fp64);
+    CUDA_TRY(cudaGetLastError());
+    return PRISM_OK;
+}
+
+prism_status prism_proj_get_factor(prism_proj_t h, double *K_host, double *kb_host)
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    if (!h->factored) return fail(PRISM_ERR_NOT_FACTORED, "prism_proj_factor has not been called");
+    if (!K_host || !kb_host) return fail(PRISM_ERR_INVALID_ARG, "null host pointer");
+    const int H = h->H, n = h->n;
+    double *Kr = (double *)malloc(sizeof(double) * n * n + sizeof(double) * n);
+    if (!Kr) return fail(PRISM_ERR_OOM, "host allocation failed");
+    double *kbr = Kr + (size_t)n * n;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(Kr, h->d_K64, sizeof(double) * n * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(kbr, h->d_kb64, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        free(Kr);
+        return fail(PRISM_ERR_CUDA, "get_factor: %s", cudaGetErrorString(e));
+    }
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < H; ++j) K_host[i * H + j] = (i == 0 || j == 0) ? 0.0 : Kr[(i - 1) * n + (j - 1)];
+    kb_host[0] = 1.0;
+    for (int i = 1; i < H; ++i) kb_host[i] = kbr[i - 1];
+    free(Kr);
+    return PRISM_OK;
+}
+
+prism_status prism_proj_query(prism_proj_t h, int batch, long long out[8])
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    if (!out) return fail(PRISM_ERR_INVALID_ARG, "out is NULL");
+    if (!h->factored) return fail(PRISM_ERR_NOT_FACTORED, "prism_proj_factor has not been called");
+    const Variant *v;
+    size_t smem;
+    int bps, grid;
+    solve_fn fn;
+    st = launch_config(h, std::max(batch, 1), v, smem, bps, grid, fn);
+    if (st) return st;
+    cudaFuncAttributes attr;
+    CUDA_TRY(cudaFuncGetAttributes(&attr, (const void *)fn));
+    const int T = std::max(1, CMAX / h->J);
+    out[0] = (long long)T * h->J;
+    out[1] = T;
+    out[2] = bps;
+    out[3] = grid;
+    out[4] = (long long)smem;
+    out[5] = attr.numRegs;
+    out[6] = v->hq;
+    out[7] = h->num_sms;
+    return PRISM_OK;
+}
+
+prism_status prism_proj_destroy(prism_proj_t h)
+{
+    if (!h) return fail(PRISM_ERR_INVALID_ARG, "null handle");
+    cudaDeviceSynchronize();
+    cudaFree(h->d_bounds);
+    cudaFree(h->d_K64);
+    cudaFree(h->d_kb64);
+    cudaFree(h->d_Kt32);
+    cudaFree(h->d_kb32);
+    cudaFree(h->d_wp);
+    cudaFree(h->d_wfull);
+    cudaFree(h->d_work);
+    cudaFree(h->d_stage);
+    delete h;
+    return PRISM_OK;
+}
+
+}  // extern "C"

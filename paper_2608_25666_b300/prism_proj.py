@@ -1,0 +1,234 @@
+"""Python binding of libprism_proj (argument marshalling only).
+
+Every step of the projection runs in the CUDA library; this module only turns
+torch tensors into device pointers and status codes into exceptions.  There is
+no CPU fallback: if the compiled library is missing, importing the symbols
+fails with an error that says how to build it.
+
+Layouts follow the C ABI (include/prism_proj.h): samples and trajectories are
+[N, H, J] float32 (time-major, joint-minor), q0 / v0 are [J] float32,
+residuals are [N, J] float32.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+MODE_ADMM, MODE_PAPER = 0, 1
+SCALE_ROWNORM, SCALE_NONE = 0, 1
+PREC_FP32, PREC_BF16X3, PREC_TF32 = 0, 1, 2
+MAX_H, MAX_J = 132, 64
+
+STATUS = {0: "PRISM_OK", 1: "PRISM_ERR_INVALID_ARG", 2: "PRISM_ERR_NOT_FACTORED",
+          3: "PRISM_ERR_RHO_MISMATCH", 4: "PRISM_ERR_INFEASIBLE_BOUNDS", 5: "PRISM_ERR_OOM",
+          6: "PRISM_ERR_CUDA", 7: "PRISM_ERR_UNSUPPORTED"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libprism_proj.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class PrismError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load the compiled library (build it with ``paper_2608_25666_b300.build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libprism_proj is not built ({LIB_PATH} missing); run "
+                                  "python -c 'import __graft_entry__ as g; g.build()'")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+            L.prism_proj_create.argtypes = [i, i, d] + [P] * 8 + [ctypes.POINTER(P)]
+            L.prism_proj_factor.argtypes = [P, d, i, i, i, P]
+            sig = [P, i, P, P, P, i, d, P, P, P, P]
+            L.prism_proj_solve.argtypes = sig
+            L.prism_proj_solve_plain.argtypes = sig
+            L.prism_proj_solve_host.argtypes = sig
+            L.prism_proj_check_fp64.argtypes = [P, i, P, P, P, P, P]
+            L.prism_proj_get_factor.argtypes = [P, P, P]
+            L.prism_proj_query.argtypes = [P, i, ctypes.POINTER(ll)]
+            L.prism_proj_destroy.argtypes = [P]
+            for name in ("create", "factor", "solve", "solve_plain", "solve_host", "check_fp64",
+                         "get_factor", "query", "destroy"):
+                getattr(L, "prism_proj_" + name).restype = i
+            L.prism_status_string.argtypes = [i]
+            L.prism_status_string.restype = ctypes.c_char_p
+            L.prism_last_error.argtypes = []
+            L.prism_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise PrismError(status, lib().prism_last_error().decode())
+
+
+def _ptr(t):
+    """Device (or host) pointer of a tensor / array, None passes NULL."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need_cuda_f32(name, t, shape):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Projector:
+    """One projector per (J, H, dt, bounds): prism_proj_create / factor / solve."""
+
+    def __init__(self, J: int, H: int, dt: float, bounds):
+        b = np.ascontiguousarray(np.asarray(bounds, dtype=np.float64).reshape(8, J))
+        self.J, self.H, self.dt = int(J), int(H), float(dt)
+        self.bounds = b
+        self._rows = [np.ascontiguousarray(b[r]) for r in range(8)]
+        h = ctypes.c_void_p()
+        _check(lib().prism_proj_create(self.J, self.H, self.dt,
+                                       *[_ptr(r) for r in self._rows], ctypes.byref(h)))
+        self._h = h
+        self.rho = None
+        self.mode = None
+
+    # ------------------------------------------------------------------
+    def factor(self, rho: float = 1.0, mode: int = MODE_ADMM, scale: int = SCALE_ROWNORM,
+               prec: int = PREC_FP32, stream=None):
+        _check(lib().prism_proj_factor(self._h, float(rho), int(mode), int(scale), int(prec),
+                                       _stream_ptr(stream)))
+        self.rho, self.mode, self.scale = float(rho), int(mode), int(scale)
+        return self
+
+    def _outputs(self, N, out, primal, dual, want_res):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            out = torch.empty((N, self.H, self.J), dtype=torch.float32, device=dev)
+        if want_res and primal is None:
+            primal = torch.empty((N, self.J), dtype=torch.float32, device=dev)
+        if want_res and dual is None:
+            dual = torch.empty((N, self.J), dtype=torch.float32, device=dev)
+        return out, primal, dual
+
+    def _solve(self, fn, q0, v0, samples, iters, rho, out, primal, dual, stream, want_res):
+        N = int(samples.shape[0])
+        _need_cuda_f32("samples", samples, (N, self.H, self.J))
+        _need_cuda_f32("q0", q0, (self.J,))
+        _need_cuda_f32("v0", v0, (self.J,))
+        out, primal, dual = self._outputs(N, out, primal, dual, want_res)
+        _need_cuda_f32("out", out, (N, self.H, self.J))
+        if primal is not None:
+            _need_cuda_f32("primal", primal, (N, self.J))
+        if dual is not None:
+            _need_cuda_f32("dual", dual, (N, self.J))
+        rho = self.rho if rho is None else rho
+        _check(fn(self._h, N, _ptr(q0), _ptr(v0), _ptr(samples), int(iters), float(rho), _ptr(out),
+                  _ptr(primal), _ptr(dual), _stream_ptr(stream)))
+        return out, primal, dual
+
+    def solve(self, q0, v0, samples, iters: int, rho: float | None = None, out=None, primal=None,
+              dual=None, stream=None, want_res: bool = True):
+        """prism_proj_solve: returns (x, primal_res, dual_res) as CUDA tensors."""
+        return self._solve(lib().prism_proj_solve, q0, v0, samples, iters, rho, out, primal, dual,
+                           stream, want_res)
+
+    def solve_plain(self, q0, v0, samples, iters: int, rho: float | None = None, out=None,
+                    primal=None, dual=None, stream=None, want_res: bool = True):
+        """prism_proj_solve_plain (the plain FP32 comparator)."""
+        return self._solve(lib().prism_proj_solve_plain, q0, v0, samples, iters, rho, out, primal,
+                           dual, stream, want_res)
+
+    def solve_host(self, q0, v0, samples, iters: int, rho: float | None = None, out=None,
+                   primal=None, dual=None, stream=None, want_res: bool = True):
+        """prism_proj_solve_host on host float32 arrays (numpy or pinned CPU tensors)."""
+        import torch
+        N = int(samples.shape[0])
+
+        def host(a, shape):
+            if isinstance(a, torch.Tensor):
+                assert a.device.type == "cpu" and a.dtype == torch.float32 and a.is_contiguous()
+                assert tuple(a.shape) == tuple(shape)
+                return a
+            a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+            assert a.shape == tuple(shape)
+            return a
+
+        samples = host(samples, (N, self.H, self.J))
+        q0 = host(q0, (self.J,))
+        v0 = host(v0, (self.J,))
+        if out is None:
+            out = np.empty((N, self.H, self.J), dtype=np.float32)
+        if want_res and primal is None:
+            primal = np.empty((N, self.J), dtype=np.float32)
+        if want_res and dual is None:
+            dual = np.empty((N, self.J), dtype=np.float32)
+        rho = self.rho if rho is None else rho
+        _check(lib().prism_proj_solve_host(self._h, N, _ptr(q0), _ptr(v0), _ptr(samples), int(iters),
+                                           float(rho), _ptr(out), _ptr(primal), _ptr(dual),
+                                           _stream_ptr(stream)))
+        return out, primal, dual
+
+    def check_fp64(self, q0, v0, x, stream=None):
+        """prism_proj_check_fp64: FP64 primal residual [N, J] (CUDA float64 tensor)."""
+        import torch
+        N = int(x.shape[0])
+        _need_cuda_f32("x", x, (N, self.H, self.J))
+        res = torch.empty((N, self.J), dtype=torch.float64, device=x.device)
+        _check(lib().prism_proj_check_fp64(self._h, N, _ptr(q0), _ptr(v0), _ptr(x), _ptr(res),
+                                           _stream_ptr(stream)))
+        return res
+
+    def get_factor(self):
+        """(K [H,H], kb [H]) in float64, copied from the device."""
+        K = np.zeros((self.H, self.H))
+        kb = np.zeros(self.H)
+        _check(lib().prism_proj_get_factor(self._h, _ptr(K), _ptr(kb)))
+        return K, kb
+
+    def query(self, batch: int) -> dict:
+        out = (ctypes.c_longlong * 8)()
+        _check(lib().prism_proj_query(self._h, int(batch), out))
+        keys = ("cols_per_tile", "samples_per_tile", "blocks_per_sm", "grid", "smem_bytes",
+                "regs_per_thread", "hq", "num_sms")
+        return dict(zip(keys, [int(v) for v in out]))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(lib().prism_proj_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
