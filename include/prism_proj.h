@@ -177,6 +177,40 @@ prism_status prism_proj_get_factor(prism_proj_t h, double *K_host, double *kb_ho
  */
 prism_status prism_proj_query(prism_proj_t h, int batch, long long out[8]);
 
+/*
+ * prism_proj_solve_plain_noalloc -- prism_proj_solve_plain for callers that
+ * must not allocate device memory when they solve.
+ *
+ * The paper has no counterpart: this is a deployment variant.  Some callers
+ * cannot call cudaMalloc at solve time: a real-time controller thread that
+ * forbids allocation after start-up (an allocation may block in the driver
+ * for an unbounded time), or a host whose device memory is owned by a pool
+ * that this library cannot see.  prism_proj_solve_plain grows a per-handle
+ * workspace with cudaMalloc on first use; this entry point instead keeps the
+ * same workspace in one fixed, file-scope device array of
+ * PRISM_NOALLOC_MAX_FLOATS floats (16 MiB) that every GPU which loads the
+ * library holds until the process exits.  It calls no cudaMalloc, cudaFree
+ * or allocating library routine.
+ *
+ *   Arguments, layouts and results are those of prism_proj_solve_plain; the
+ *   handle must already be factored (create and factor allocate, so callers
+ *   do them at start-up).  The workspace needs batch * J * 6 * H floats;
+ *   larger requests return PRISM_ERR_INVALID_ARG before anything is enqueued.
+ *   The first call on each device looks up the device address of the array
+ *   (cudaGetSymbolAddress, with that device current) and caches it; make
+ *   that first call before any stream capture begins.
+ *   All calls share the one array and it keeps the last call's contents; the
+ *   kernel writes every workspace entry it reads, so nothing has to be
+ *   cleared, but calls whose work overlaps on the GPU (different streams or
+ *   handles, no ordering between them) race on the array.  Order them on one
+ *   stream or with events.
+ */
+#define PRISM_NOALLOC_MAX_FLOATS 4194304
+prism_status prism_proj_solve_plain_noalloc(prism_proj_t h, int batch, const float *q0,
+                                            const float *v0, const float *samples, int iters,
+                                            double rho, float *out, float *primal_res,
+                                            float *dual_res, void *cuda_stream);
+
 /* prism_proj_destroy -- free the handle and its device memory (synchronises the device). */
 prism_status prism_proj_destroy(prism_proj_t h);
 

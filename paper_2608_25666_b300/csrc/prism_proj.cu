@@ -41,6 +41,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cstdint>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -880,6 +881,35 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Fixed workspace of prism_proj_solve_plain_noalloc: one file-scope device
+// array (PRISM_NOALLOC_MAX_FLOATS floats per device), shared by all calls.
+// In host code g_noalloc_scratch is only a stand-in symbol; its device
+// address comes from cudaGetSymbolAddress with the device current.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) float g_noalloc_scratch[PRISM_NOALLOC_MAX_FLOATS];
+
+namespace {
+constexpr int kMaxDevices = 128;
+std::mutex g_noalloc_mu;
+float *g_noalloc_addr[kMaxDevices] = {};
+
+prism_status noalloc_scratch(int device, float **out)
+{
+    if (device < 0 || device >= kMaxDevices) return fail(PRISM_ERR_UNSUPPORTED, "device ordinal %d", device);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(PRISM_ERR_CUDA, "cudaGetSymbolAddress(noalloc scratch): %s", cudaGetErrorString(e));
+        g_noalloc_addr[device] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return PRISM_OK;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -1044,6 +1074,35 @@ prism_status prism_proj_solve_plain(prism_proj_t h, int batch, const float *q0, 
         plain_kernel<PRISM_MODE_ADMM><<<(unsigned)blocks, tpb, 0, (cudaStream_t)cuda_stream>>>(p, h->d_work, ncols);
     else
         plain_kernel<PRISM_MODE_PAPER><<<(unsigned)blocks, tpb, 0, (cudaStream_t)cuda_stream>>>(p, h->d_work, ncols);
+    CUDA_TRY(cudaGetLastError());
+    return PRISM_OK;
+}
+
+prism_status prism_proj_solve_plain_noalloc(prism_proj_t h, int batch, const float *q0, const float *v0,
+                                            const float *samples, int iters, double rho, float *out,
+                                            float *primal_res, float *dual_res, void *cuda_stream)
+{
+    SolveParams p;
+    prism_status st = prepare_solve(h, batch, q0, v0, samples, iters, rho, out, p);
+    if (st) return st;
+    if (batch == 0) return PRISM_OK;
+    p.primal = primal_res;
+    p.dual = dual_res;
+    const long long ncols = (long long)batch * h->J;
+    const long long need = ncols * 6LL * h->H;
+    if (need > (long long)PRISM_NOALLOC_MAX_FLOATS)
+        return fail(PRISM_ERR_INVALID_ARG,
+                    "noalloc workspace: batch*J*6*H = %lld floats exceeds the fixed %d-float array", need,
+                    PRISM_NOALLOC_MAX_FLOATS);
+    float *scratch = nullptr;
+    st = noalloc_scratch(h->device, &scratch);
+    if (st) return st;
+    const int tpb = 128;
+    const long long blocks = (ncols + tpb - 1) / tpb;
+    if (h->mode == PRISM_MODE_ADMM)
+        plain_kernel<PRISM_MODE_ADMM><<<(unsigned)blocks, tpb, 0, (cudaStream_t)cuda_stream>>>(p, scratch, ncols);
+    else
+        plain_kernel<PRISM_MODE_PAPER><<<(unsigned)blocks, tpb, 0, (cudaStream_t)cuda_stream>>>(p, scratch, ncols);
     CUDA_TRY(cudaGetLastError());
     return PRISM_OK;
 }
