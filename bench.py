@@ -32,6 +32,7 @@ WORKLOAD = workloads.WORKLOADS["realistic"]
 METRIC = "projected trajectories/s"
 UNIT = "trajectories/s"
 N_INPUTS = 64
+PRECS = {"fp32": 0, "tf32x3": 3}
 
 
 def flops_per_column_iteration(H: int) -> int:
@@ -194,7 +195,7 @@ def run_reference(args):
 def config_dict():
     w = WORKLOAD
     return {"workload": f"realistic single MPC step: N={w.N} samples, J={w.J} joints, H={w.H}, "
-                        f"dt={w.dt}, {w.iters} iterations, rho={w.rho}, ADMM, row-normalised, FP32",
+                        f"dt={w.dt}, {w.iters} iterations, rho={w.rho}, ADMM, row-normalised",
             "N": w.N, "J": w.J, "H": w.H, "dt": w.dt, "iters": w.iters,
             "l2": f"inputs larger than L2: {N_INPUTS} distinct step inputs cycled "
                   f"({N_INPUTS * w.N * w.H * w.J * 4 / 1e6:.0f} MB)"}
@@ -209,6 +210,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=32)
+    ap.add_argument("--prec", default="tf32x3", choices=list(PRECS))
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -232,7 +234,9 @@ def main():
     outs = [torch.empty_like(xs[0]) for _ in range(N_INPUTS)]
     prs = torch.empty((N_INPUTS, w.N, w.J), device=dev)
     dus = torch.empty((N_INPUTS, w.N, w.J), device=dev)
-    P = pp.Projector(w.J, w.H, w.dt, bounds).factor(w.rho, pp.MODE_ADMM, pp.SCALE_ROWNORM)
+    prec = PRECS[args.prec]
+    P = pp.Projector(w.J, w.H, w.dt, bounds).factor(w.rho, pp.MODE_ADMM, pp.SCALE_ROWNORM, prec)
+    Pplain = pp.Projector(w.J, w.H, w.dt, bounds).factor(w.rho, pp.MODE_ADMM, pp.SCALE_ROWNORM)
     q = P.query(w.N)
     stream = torch.cuda.current_stream()
 
@@ -270,13 +274,13 @@ def main():
     # ---- plain FP32 comparator on the same inputs
     for s in range(3):
         k = s % N_INPUTS
-        P.solve_plain(q0s[k], v0s[k], xs[k], w.iters, out=outs[k], primal=prs[k], dual=dus[k])
+        Pplain.solve_plain(q0s[k], v0s[k], xs[k], w.iters, out=outs[k], primal=prs[k], dual=dus[k])
     torch.cuda.synchronize()
     pe = [torch.cuda.Event(enable_timing=True) for _ in range(args.plain_steps + 1)]
     pe[0].record(stream)
     for s in range(args.plain_steps):
         k = s % N_INPUTS
-        P.solve_plain(q0s[k], v0s[k], xs[k], w.iters, out=outs[k], primal=prs[k], dual=dus[k])
+        Pplain.solve_plain(q0s[k], v0s[k], xs[k], w.iters, out=outs[k], primal=prs[k], dual=dus[k])
         pe[s + 1].record(stream)
     torch.cuda.synchronize()
     plain_ms = [pe[s].elapsed_time(pe[s + 1]) for s in range(args.plain_steps)]
@@ -308,7 +312,7 @@ def main():
     peak = peak_fp32_tflops(q["num_sms"], 2032.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "solve_kernel (persistent ADMM, FP32 SIMT)",
+                "kernel": f"solve_kernel (persistent ADMM, K-apply {args.prec})",
                 "peak_basis": f"FP32 FMA issue rate {q['num_sms']} SMs x 128 lanes x 2 flop x 2032 MHz"
                               " (max SM clock; derived, no measured FP32 peak)",
                 "algorithmic_flops_per_launch": flops,
@@ -322,7 +326,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
                 "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.prec == "fp32" else "f32 (K-apply: tf32 split on tensor cores, f32 accumulate)",
                 "data": "synthetic (seeded white-noise samples; no dataset)",
                 "config": config_dict(),
                 "latency_ms": {"p50": p50, "p99": p99, "max": max(per_step_ms)},
@@ -341,6 +346,7 @@ def main():
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     P.close()
+    Pplain.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

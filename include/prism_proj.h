@@ -75,7 +75,13 @@ typedef enum {
 
 enum { PRISM_MODE_ADMM = 0, PRISM_MODE_PAPER = 1 };
 enum { PRISM_SCALE_ROWNORM = 0, PRISM_SCALE_NONE = 1 };
-enum { PRISM_PREC_FP32 = 0, PRISM_PREC_BF16X3 = 1, PRISM_PREC_TF32 = 2 };
+/* K-apply precision: FP32 on the FP32 pipe; TF32X3 on the tensor cores with
+ * both operands split into a tf32 high part and a remainder (products of all
+ * parts, FP32 accumulation: FP32-level accuracy); TF32 on the tensor cores with
+ * the high parts only, except for the last polish_iters iterations
+ * (prism_solve_opts), which use the split.  BF16X3 is reserved and returns
+ * PRISM_ERR_UNSUPPORTED in this build. */
+enum { PRISM_PREC_FP32 = 0, PRISM_PREC_BF16X3 = 1, PRISM_PREC_TF32 = 2, PRISM_PREC_TF32X3 = 3 };
 
 #define PRISM_MAX_H 132   /* horizon limit of the on-chip solve kernel          */
 #define PRISM_MAX_J 64    /* joints per sample handled by one thread block       */
@@ -104,8 +110,10 @@ prism_status prism_proj_create(int J, int H, double dt,
  *   for PAPER, where G^T G = 2 F^T F), Cholesky-factors the block acting on
  *   x_2..x_H, eliminates the equality x_1 = v0, and keeps K = [M^-1]_{1:H,1:H}
  *   and kb = [M^-1]_{1:H,H+1} on the device (FP64, plus an FP32 copy used by
- *   the solve).  rho > 0 is the paper's penalty delta.  prec must be
- *   PRISM_PREC_FP32 in this build (others: PRISM_ERR_UNSUPPORTED).  Enqueued on
+ *   the solve).  rho > 0 is the paper's penalty delta.  prec selects the
+ *   K-apply of prism_proj_solve: PRISM_PREC_FP32 (FP32 pipe, any H) or
+ *   PRISM_PREC_TF32X3 / PRISM_PREC_TF32 (tensor cores, H <= 105; larger H
+ *   returns PRISM_ERR_UNSUPPORTED).  Enqueued on
  *   cuda_stream; re-factoring a handle replaces its factor (the caller orders
  *   it after solves that still use the old one).
  */
@@ -132,6 +140,33 @@ prism_status prism_proj_solve(prism_proj_t h, int batch, const float *q0, const 
                               float *primal_res, float *dual_res, void *cuda_stream);
 
 /*
+ * prism_proj_solve_ex -- prism_proj_solve with a warm start and state export.
+ *   opts may be NULL (then identical to prism_proj_solve).  Fields:
+ *   x_init    device float [N][H][J] initial iterate, or NULL for x^0 = xi;
+ *             x_1 is always reset to v0; must not alias out
+ *   dual_init device float [N][D][J] initial multiplier, or NULL for 0
+ *   dual_out  device float [N][D][J] multiplier after the last iteration, or NULL
+ *   polish_iters  for PRISM_PREC_TF32: how many final iterations use the split
+ *             (FP32-accurate) K-apply; ignored for other precisions
+ *   D = 4H-1 in ADMM mode: the multiplier of the row-normalised two-sided rows
+ *   in the order velocity k=1..H, position k=1..H, acceleration k=1..H, jerk
+ *   k=2..H (the scaled ADMM multiplier u of the oracle, same units under
+ *   PRISM_SCALE_ROWNORM; under PRISM_SCALE_NONE the printed rows' units);
+ *   D = H in PAPER mode: lambda of Eq. admm_dual.
+ */
+typedef struct {
+    const float *x_init;
+    const float *dual_init;
+    float *dual_out;
+    int polish_iters;
+} prism_solve_opts;
+
+prism_status prism_proj_solve_ex(prism_proj_t h, int batch, const float *q0, const float *v0,
+                                 const float *samples, int iters, double rho,
+                                 const prism_solve_opts *opts, float *out, float *primal_res,
+                                 float *dual_res, void *cuda_stream);
+
+/*
  * prism_proj_solve_plain -- the same projection computed by the plain FP32
  * comparator: one thread per column, the iteration state in a device
  * workspace that the handle allocates on first use (and grows), the cached
@@ -153,6 +188,19 @@ prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_ho
                                    const float *v0_host, const float *samples_host, int iters,
                                    double rho, float *out_host, float *primal_res_host,
                                    float *dual_res_host, void *cuda_stream);
+
+/*
+ * prism_proj_shift_state -- receding-horizon shift of a warm start (in place).
+ *   For every column, each block of the state moves `steps` entries earlier and
+ *   the block's last entry fills the tail: x [N][H][J] (may be NULL) and the
+ *   multiplier dual [N][D][J] of prism_proj_solve_ex (may be NULL; ADMM blocks:
+ *   velocity H, position H, acceleration H, jerk H-1 rows; PAPER: one block of
+ *   H).  The paper shifts its sampling distribution between MPC steps the same
+ *   way (Sec. III-B); shifting the multiplier is this library's reading.
+ *   steps >= 0; steps >= H leaves every block filled with its last entry.
+ */
+prism_status prism_proj_shift_state(prism_proj_t h, int batch, int steps, float *x, float *dual,
+                                    void *cuda_stream);
 
 /*
  * prism_proj_check_fp64 -- the final feasibility check in FP64 on the GPU:

@@ -118,6 +118,8 @@ struct prism_proj_s {
     float *d_Kt32 = nullptr;             // [n][MP] transposed K, FP32, zero padded
     float *d_kb32 = nullptr;             // [MP]
     float *d_wp = nullptr;               // [PRISM_MAX_H] position-row weights
+    float *d_Khi = nullptr, *d_Klo = nullptr;   // [n][n] tf32 split of K'
+    int *d_err = nullptr;                // tensor-core wait timeout flag
     double *d_wfull = nullptr;           // factor input: per-row weights (4 blocks x H)
     // plain comparator workspace
     float *d_work = nullptr;
@@ -142,7 +144,8 @@ __device__ __forceinline__ double d2c(int m, int i)
 
 __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wrow,
                               double *__restrict__ K64, double *__restrict__ kb64,
-                              float *__restrict__ Kt32, float *__restrict__ kb32, int MP)
+                              float *__restrict__ Kt32, float *__restrict__ kb32, int MP,
+                              float *__restrict__ Khi32, float *__restrict__ Klo32)
 {
     extern __shared__ double Bs[];   // H*H
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -204,6 +207,16 @@ __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wr
         const int j = e / MP, i = e % MP;
         Kt32[e] = (i < n) ? (float)K64[i * n + j] : 0.0f;
     }
+    // tf32 split of K' for the tensor-core K-apply: hi = K' rounded to tf32,
+    // lo = the remainder in FP32 (the tensor core keeps its leading tf32 bits).
+    for (int e = tid; e < n * n; e += nth) {
+        uint32_t r;
+        const float kf = (float)K64[e];
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(kf));
+        const float hi = __uint_as_float(r);
+        Khi32[e] = hi;
+        Klo32[e] = (float)(K64[e] - (double)hi);
+    }
 }
 
 // ===========================================================================
@@ -221,6 +234,14 @@ struct SolveParams {
     const float *__restrict__ Kt;        // [n][MP]
     const float *__restrict__ kb;        // [MP]
     const float *__restrict__ wp;        // [>= H]
+    const float *__restrict__ Khi;       // [n][n] tf32 high part of K' (tensor-core path)
+    const float *__restrict__ Klo;       // [n][n] remainder K' - Khi
+    int *err;                            // set to 1 if a tensor-core wait ran out
+    const float *x_init;                 // [N][H][J] warm-start iterate or NULL (x^0 = xi)
+    const float *dual_init;              // [N][D][J] warm-start multiplier or NULL (0)
+    float *dual_out;                     // [N][D][J] final multiplier or NULL
+    int polish;                          // tensor cores: last iterations with the split K-apply
+    int D;                               // multiplier rows per column: 4H-1 (ADMM) or H (PAPER)
     float *out;
     float *primal;
     float *dual;
@@ -392,43 +413,190 @@ __device__ __forceinline__ void kapply(float *__restrict__ xs, const float *__re
 }
 
 // ===========================================================================
+// tcgen05 helpers (Blackwell tensor cores, accumulator in tensor memory).
+// Operands are K-major, no swizzle: element (r, k) of an R x KD tf32 matrix
+// lives at byte ((r/8)*(KD/4) + k/4)*128 + (r%8)*16 + (k%4)*4, i.e. 8-row x
+// 16-byte core matrices, K-adjacent ones 128 B apart (LBO), 8-row groups
+// (KD/4)*128 B apart (SBO).
+// ===========================================================================
+__host__ __device__ __forceinline__ int cm_off(int r, int k, int KD)
+{
+    return ((r >> 3) * (KD >> 2) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of tcgen05; no swizzle, base offset 0
+    return d;
+}
+
+// kind::tf32 instruction descriptor: D f32, A and B tf32, both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int m, int n)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_rna(float v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
+}
+
+// Bounded wait on an mbarrier phase; returns false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+__host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// TC operand sizes for reduced size n = H - 1.
+__host__ __device__ inline int tc_kd(int n) { return round_up(n, 8); }
+__host__ __device__ inline int tc_ndim(int n) { return round_up(n, 16); }
+__host__ __device__ inline int tc_tmem_cols(int n)
+{
+    const int nd = tc_ndim(n);
+    return nd <= 32 ? 32 : nd <= 64 ? 64 : nd <= 128 ? 128 : 256;
+}
+
+// ===========================================================================
 // K3: persistent solve.  HQ = horizon steps per thread (H <= 4*HQ), MODE =
-// PRISM_MODE_ADMM / PRISM_MODE_PAPER.
-// Shared memory (floats): xs[(4HQ+2) x CP] (rows: x_{-2}, x_{-1}, x_0 .. ),
-// rhs[4HQ x CP], Kt[n x MP], kb[MP], wp[4HQ], v0c[CMAX], dres[CMAX].
+// PRISM_MODE_ADMM / PRISM_MODE_PAPER, TC = K-apply on the tensor cores.
+// Shared memory: xs[(4HQ+2) x CP] floats (rows x_{-2}, x_{-1}, x_0 ..), rhs
+// [4HQ x CP], kb, wp, v0c, dres; the FP32-pipe variant adds Kt[n x MP]; the
+// tensor-core variant adds the operands A (128 x KD: the tile's right-hand
+// sides, tf32 high parts in rows 0..63, remainders in rows 64..127) and B
+// (K' high and low parts, ND x KD each) and keeps D (128 x ND fp32) in tensor
+// memory.  Summing both halves of D gives K'(rhs_hi + rhs_lo) with the
+// products of the two tf32 parts of both operands, i.e. FP32-level accuracy.
 // ===========================================================================
 template <int HQ>
 __host__ __device__ constexpr int solve_min_blocks() { return HQ <= 17 ? 2 : 1; }
 
-template <int HQ, int MODE>
+// Shared-memory carve-up of the solve kernel (byte offsets).
+struct SolveSmem {
+    int a, bhi, blo, xs, rhs, kt, kb, wp, v0c, dres, total;
+};
+
+__host__ __device__ inline SolveSmem solve_smem(int hq, int n, int MP, bool tc)
+{
+    const int HP = 4 * hq, CP = col_stride(hq);
+    SolveSmem L;
+    int off = 0;
+    if (tc) {
+        const int KD = tc_kd(n), ND = tc_ndim(n);
+        L.a = off;   off += 128 * KD * 4;
+        L.bhi = off; off += ND * KD * 4;
+        L.blo = off; off += ND * KD * 4;
+    } else {
+        L.a = L.bhi = L.blo = 0;
+    }
+    L.xs = off;  off += (HP + 2) * CP * 4;
+    L.rhs = off; off += HP * CP * 4;          // SIMT: rhs; tensor cores: lower-half partial sums
+    L.kt = off;  off += tc ? 0 : n * MP * 4;
+    L.kb = off;  off += MP * 4;
+    L.wp = off;  off += HP * 4;
+    L.v0c = off; off += CMAX * 4;
+    L.dres = off; off += CMAX * 4;
+    L.total = off;
+    return L;
+}
+
+template <int HQ, int MODE, bool TC>
 __global__ void __launch_bounds__(NTHREADS, solve_min_blocks<HQ>())
 solve_kernel(const SolveParams p)
 {
     constexpr int HP = 4 * HQ;
     constexpr int CP = col_stride(HQ);
-    extern __shared__ float4 smem4[];
-    float *xs = reinterpret_cast<float *>(smem4);
-    float *rhs = xs + (HP + 2) * CP;
-    float *Kts = rhs + HP * CP;
-    float *kbs = Kts + p.n * p.MP;
-    float *wps = kbs + p.MP;
-    float *v0c = wps + HP;
-    unsigned *dres = reinterpret_cast<unsigned *>(v0c + CMAX);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mma_bar;
+    const SolveSmem L = solve_smem(HQ, p.n, p.MP, TC);
+    float *xs = reinterpret_cast<float *>(smem_raw + L.xs);
+    float *rhs = reinterpret_cast<float *>(smem_raw + L.rhs);
+    float *Kts = reinterpret_cast<float *>(smem_raw + L.kt);
+    float *kbs = reinterpret_cast<float *>(smem_raw + L.kb);
+    float *wps = reinterpret_cast<float *>(smem_raw + L.wp);
+    float *v0c = reinterpret_cast<float *>(smem_raw + L.v0c);
+    unsigned *dres = reinterpret_cast<unsigned *>(smem_raw + L.dres);
+    unsigned char *As = smem_raw + L.a;
 
     const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
     const int c = tid >> 2;       // column in tile
     const int b = tid & 3;        // time quarter
     const int i0 = b * HQ;
     const int H = p.H, J = p.J, n = p.n;
     const int HJ = H * J;
     const float rho = p.rho;
+    const int KD = tc_kd(n), ND = tc_ndim(n);
 
     // per-shape constants -> shared memory (once)
-    for (int e = tid; e < n * p.MP; e += NTHREADS) Kts[e] = p.Kt[e];
+    if (!TC)
+        for (int e = tid; e < n * p.MP; e += NTHREADS) Kts[e] = p.Kt[e];
     for (int e = tid; e < p.MP; e += NTHREADS) kbs[e] = p.kb[e];
     for (int e = tid; e < HP; e += NTHREADS) wps[e] = (e < H) ? p.wp[e] : 0.0f;
+    uint32_t tbase = 0, mma_phase = 0;
+    if (TC) {
+        // B = K' (rows i, reduction j) split in tf32 high / low parts; A zeroed
+        // once (its padding columns k >= n stay zero).
+        for (int e = tid; e < ND * KD; e += NTHREADS) {
+            const int i = e / KD, j = e - i * KD;
+            const bool in = i < n && j < n;
+            *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(i, j, KD)) = in ? p.Khi[i * n + j] : 0.0f;
+            *reinterpret_cast<float *>(smem_raw + L.blo + cm_off(i, j, KD)) = in ? p.Klo[i * n + j] : 0.0f;
+        }
+        for (int e = tid; e < 128 * KD; e += NTHREADS) reinterpret_cast<float *>(As)[e] = 0.0f;
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         :: "r"(smem_addr(&tmem_slot)), "r"(tc_tmem_cols(n)));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mma_bar)));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tbase = tmem_slot;
+    }
+    bool aborted = false;
 
-    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+    for (int tile = blockIdx.x; tile < p.ntiles && !aborted; tile += gridDim.x) {
         const int n0 = tile * p.T;
         const int Tt = min(p.T, p.N - n0);
         const int Ct = Tt * J;
@@ -443,7 +611,7 @@ solve_kernel(const SolveParams p)
         }
         __syncthreads();
         {
-            const float *src = p.xi + (size_t)n0 * HJ;
+            const float *src = (p.x_init ? p.x_init : p.xi) + (size_t)n0 * HJ;
             const int total = Tt * HJ;
             for (int e = tid; e < total; e += NTHREADS) {
                 const int nl = e / HJ, rem = e - nl * HJ;
@@ -455,11 +623,18 @@ solve_kernel(const SolveParams p)
         // ---- a2: per-column bounds in registers; xi quarter in registers; x_0 := v0
         const bool colv = c < Ct;
         const int jj = colv ? (c % J) : 0;
+        const int nl_c = colv ? (c / J) : 0;
         const float q0j = p.q0[jj], v0j = p.v0[jj];
         const ColBounds cb = col_bounds(p.bounds, J, jj, p.dt, q0j, v0j);
         float xi[HQ];
+        if (p.x_init) {
+            const float *src = p.xi + (size_t)(n0 + nl_c) * HJ + jj;
 #pragma unroll
-        for (int r = 0; r < HQ; ++r) xi[r] = xs[(i0 + r + 2) * CP + c];
+            for (int r = 0; r < HQ; ++r) xi[r] = (colv && i0 + r < H) ? __ldg(src + (size_t)(i0 + r) * J) : 0.0f;
+        } else {
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) xi[r] = xs[(i0 + r + 2) * CP + c];
+        }
         __syncthreads();
         if (b == 0) xs[2 * CP + c] = colv ? v0j : 0.0f;
         __syncthreads();
@@ -483,13 +658,35 @@ solve_kernel(const SolveParams p)
                 t_j[r] = (vi && i >= 1) ? ya - (X.w[r + 1] - X.w[r]) : 0.0f;
                 lam[r] = 0.0f;
             }
+            if (p.dual_init && colv) {
+                // warm-start multiplier: u' (scaled rows, the oracle's units) -> u = u'/sqrt(w)
+                // in the device units, t = y - u.  PAPER mode: lambda as is.
+                const size_t base = (size_t)(n0 + nl_c) * p.D * J + jj;
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    if (i < H) {
+                        if (MODE == PRISM_MODE_ADMM) {
+                            t_v[r] -= __ldg(p.dual_init + base + (size_t)i * J) * rsqrtf(p.wv);
+                            t_p[r] -= __ldg(p.dual_init + base + (size_t)(H + i) * J) * rsqrtf(wps[i]);
+                            t_a[r] -= __ldg(p.dual_init + base + (size_t)(2 * H + i) * J) *
+                                      rsqrtf(i == 0 ? p.wa0 : p.wa);
+                            if (i >= 1)
+                                t_j[r] -= __ldg(p.dual_init + base + (size_t)(3 * H + i - 1) * J) *
+                                          rsqrtf(i == 1 ? p.wj0 : p.wj);
+                        } else {
+                            lam[r] = __ldg(p.dual_init + base + (size_t)i * J);
+                        }
+                    }
+                }
+            }
         }
 
         for (int l = 0; l < p.iters; ++l) {
-            // ---- stencil phase: a3 slack / clip, a4 Fh^T, a6 multiplier, rhs
+            // ---- stencil phase: a3 slack / clip, a4 Fh^T, a6 multiplier -> rhs
             if (l > 0) load_xwin<HQ>(xs, CP, c, b, X);
             Rows<HQ> s;
-            float g[HQ];
+            float g[HQ], rv[HQ];
             if (MODE == PRISM_MODE_ADMM) {
                 float cs = X.pre;
 #pragma unroll
@@ -517,10 +714,7 @@ solve_kernel(const SolveParams p)
                 }
                 apply_FT<HQ>(s, b, g);
 #pragma unroll
-                for (int r = 0; r < HQ; ++r) {
-                    const int i = i0 + r;
-                    if (i >= 1 && i < H) rhs[i * CP + c] = fmaf(rho, g[r], xi[r]);
-                }
+                for (int r = 0; r < HQ; ++r) rv[r] = fmaf(rho, g[r], xi[r]);
             } else {
                 if (l > 0) {   // complete lambda <- lambda~ - rho Fh^T W y^l
                     float cs = X.pre;
@@ -560,16 +754,101 @@ solve_kernel(const SolveParams p)
                 apply_FT<HQ>(s, b, g);
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
-                    const int i = i0 + r;
-                    if (i >= 1 && i < H) rhs[i * CP + c] = fmaf(rho, g[r], lam[r] + xi[r]);
+                    rv[r] = fmaf(rho, g[r], lam[r] + xi[r]);
                     lam[r] = fmaf(0.5f * rho, g[r], lam[r]);
                 }
             }
-            __syncthreads();
-            // ---- a5: K-apply
-            kapply(xs, rhs, Kts, kbs, v0c, dres, n, p.MP, CP, ncg, l == p.iters - 1);
-            __syncthreads();
+            const bool last = (l == p.iters - 1);
+            if (!TC) {
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    if (i >= 1 && i < H) rhs[i * CP + c] = rv[r];
+                }
+                __syncthreads();
+                // ---- a5: K-apply on the FP32 pipe
+                kapply(xs, rhs, Kts, kbs, v0c, dres, n, p.MP, CP, ncg, last);
+                __syncthreads();
+            } else {
+                // rhs -> A (rows c: tf32 high part, rows 64 + c: remainder), K = i - 1.
+                // Iterations before the polish phase use the high parts only.
+                const bool split = l >= p.iters - p.polish;
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    if (i >= 1 && i < H) {
+                        const float hi = tf32_rna(rv[r]);
+                        *reinterpret_cast<float *>(As + cm_off(c, i - 1, KD)) = hi;
+                        *reinterpret_cast<float *>(As + cm_off(CMAX + c, i - 1, KD)) = split ? rv[r] - hi : 0.0f;
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                // ---- a5: K-apply on the tensor cores: D[c'][i] = sum_j A[c'][j] (Khi + Klo)[i][j]
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t idesc = umma_idesc_tf32(128, ND);
+                    const uint32_t a0 = smem_addr(As), bh = smem_addr(smem_raw + L.bhi), bl = smem_addr(smem_raw + L.blo);
+                    const uint32_t sbo = (uint32_t)(KD >> 2) * 128u;
+                    for (int ks = 0; ks < (KD >> 3); ++ks) {
+                        const uint32_t koff = (uint32_t)ks * 256u;
+                        const uint64_t ad = umma_desc(a0 + koff, 128u, sbo);
+                        umma_tf32(tbase, ad, umma_desc(bh + koff, 128u, sbo), idesc, ks > 0 ? 1u : 0u);
+                        if (split) umma_tf32(tbase, ad, umma_desc(bl + koff, 128u, sbo), idesc, 1u);
+                    }
+                    umma_commit(smem_addr(&mma_bar));
+                }
+                const bool ok = mbar_wait(smem_addr(&mma_bar), mma_phase);
+                mma_phase ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0 && p.err) atomicExch(p.err, 1);
+                    aborted = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // readback: warp quarter q holds TMEM lanes 32q..32q+31; lanes 0..63 are
+                // the high-part rows (column c), 64..127 the remainder rows.
+                const int q = warp & 3, half = warp >> 2;
+                const int cc = 32 * (q & 1) + lane;
+                const int NH = ND >> 1;
+                const uint32_t tl = tbase + ((uint32_t)(32 * q) << 16);
+                if (q >= 2) {
+                    for (int ch = 0; ch < NH; ch += 8) {
+                        float d[8];
+                        tmem_ld8(tl + (uint32_t)(half * NH + ch), d);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int i = half * NH + ch + e;
+                            if (i < n) rhs[i * CP + cc] = d[e];
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+                if (q < 2) {
+                    const float v0v = v0c[cc];
+                    float dm = 0.0f;
+                    for (int ch = 0; ch < NH; ch += 8) {
+                        float d[8];
+                        tmem_ld8(tl + (uint32_t)(half * NH + ch), d);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int i = half * NH + ch + e;
+                            if (i < n) {
+                                const float nv = fmaf(kbs[i], v0v, d[e] + rhs[i * CP + cc]);
+                                float *dst = xs + (i + 3) * CP + cc;
+                                if (last) dm = fmaxf(dm, fabsf(nv - *dst));
+                                *dst = nv;
+                            }
+                        }
+                    }
+                    if (last) atomicMax(&dres[cc], __float_as_uint(dm));
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+            }
         }
+        if (aborted) break;
 
         // ---- a7: residuals and store
         load_xwin<HQ>(xs, CP, c, b, X);
@@ -596,6 +875,52 @@ solve_kernel(const SolveParams p)
                 }
             }
         }
+        if (p.dual_out) {
+            // final multiplier in the oracle's units: ADMM u' = sqrt(w) (y - t); PAPER
+            // lambda^L = lambda~ - rho Fh^T W y^L
+            const size_t base = (size_t)(n0 + nl_c) * p.D * J + jj;
+            if (MODE == PRISM_MODE_ADMM) {
+                float cs = X.pre;
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    cs += X.w[r + 2];
+                    if (colv && i < H) {
+                        const float ya = X.w[r + 2] - X.w[r + 1];
+                        const float yj = ya - (X.w[r + 1] - X.w[r]);
+                        p.dual_out[base + (size_t)i * J] = sqrtf(p.wv) * (X.w[r + 2] - t_v[r]);
+                        p.dual_out[base + (size_t)(H + i) * J] = sqrtf(wps[i]) * (cs - t_p[r]);
+                        p.dual_out[base + (size_t)(2 * H + i) * J] = sqrtf(i == 0 ? p.wa0 : p.wa) * (ya - t_a[r]);
+                        if (i >= 1)
+                            p.dual_out[base + (size_t)(3 * H + i - 1) * J] =
+                                sqrtf(i == 1 ? p.wj0 : p.wj) * (yj - t_j[r]);
+                    }
+                }
+            } else {
+                Rows<HQ> s;
+                float g[HQ];
+                float cs = X.pre;
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    const bool vi = colv && i < H;
+                    cs += X.w[r + 2];
+                    const float ya = X.w[r + 2] - X.w[r + 1];
+                    const float yj = ya - (X.w[r + 1] - X.w[r]);
+                    s.v[r] = vi ? p.wv * X.w[r + 2] : 0.0f;
+                    s.p[r] = vi ? wps[i] * cs : 0.0f;
+                    s.a[r] = vi ? ((i == 0) ? p.wa0 : p.wa) * ya : 0.0f;
+                    s.j[r] = (vi && i >= 1) ? ((i == 1) ? p.wj0 : p.wj) * yj : 0.0f;
+                }
+                apply_FT<HQ>(s, b, g);
+                const bool any = p.iters > 0;
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    if (colv && i < H) p.dual_out[base + (size_t)i * J] = any ? fmaf(-rho, g[r], lam[r]) : lam[r];
+                }
+            }
+        }
         viol = fmaxf(viol, __shfl_xor_sync(0xffffffffu, viol, 1, 4));
         viol = fmaxf(viol, __shfl_xor_sync(0xffffffffu, viol, 2, 4));
         if (b == 0 && colv) {
@@ -612,6 +937,12 @@ solve_kernel(const SolveParams p)
                 dst[e] = xs[(k + 2) * CP + nl * J + j];
             }
         }
+    }
+    if (TC) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(tc_tmem_cols(n)));
     }
 }
 
@@ -756,6 +1087,39 @@ __global__ void __launch_bounds__(128) plain_kernel(const SolveParams p, float *
 }
 
 // ===========================================================================
+// K7: receding-horizon shift of a warm-start state.  One thread per column
+// moves every block of the state s steps earlier and repeats the block's last
+// entry at the tail (the paper shifts the sampling distribution the same way
+// between MPC steps, Sec. III-B).
+// ===========================================================================
+__global__ void shift_kernel(long long ncols, int J, int H, int D, int mode, int s, float *__restrict__ x,
+                             float *__restrict__ dual)
+{
+    const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    const long long nn = col / J;
+    const int j = (int)(col % J);
+    auto shift_block = [&](float *base, int len) {
+        for (int k = 0; k < len; ++k) {
+            const int src = min(k + s, len - 1);
+            base[(size_t)k * J] = base[(size_t)src * J];
+        }
+    };
+    if (x) shift_block(x + (size_t)nn * H * J + j, H);
+    if (dual) {
+        float *d = dual + (size_t)nn * D * J + j;
+        if (mode == PRISM_MODE_ADMM) {
+            shift_block(d, H);
+            shift_block(d + (size_t)H * J, H);
+            shift_block(d + (size_t)2 * H * J, H);
+            shift_block(d + (size_t)3 * H * J, H - 1);
+        } else {
+            shift_block(d, H);
+        }
+    }
+}
+
+// ===========================================================================
 // K5: FP64 feasibility check, written from the derivative definitions.
 // ===========================================================================
 __global__ void check_kernel(int N, int J, int H, double dt, const double *__restrict__ bnd,
@@ -799,10 +1163,12 @@ typedef void (*solve_fn)(const SolveParams);
 
 struct Variant {
     int hq;
-    solve_fn admm, paper;
+    solve_fn admm, paper, admm_tc, paper_tc;
 };
 
-#define VARIANT(HQv) {HQv, solve_kernel<HQv, PRISM_MODE_ADMM>, solve_kernel<HQv, PRISM_MODE_PAPER>}
+#define VARIANT(HQv)                                                                              \
+    {HQv, solve_kernel<HQv, PRISM_MODE_ADMM, false>, solve_kernel<HQv, PRISM_MODE_PAPER, false>, \
+     solve_kernel<HQv, PRISM_MODE_ADMM, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true>}
 const Variant kVariants[] = {VARIANT(3), VARIANT(5), VARIANT(7), VARIANT(9), VARIANT(11),
                              VARIANT(13), VARIANT(15), VARIANT(17), VARIANT(21), VARIANT(25),
                              VARIANT(29), VARIANT(33)};
@@ -815,11 +1181,13 @@ const Variant *pick_variant(int H)
     return nullptr;
 }
 
-size_t solve_smem_bytes(int hq, int n, int MP)
+// The tensor-core variant needs its operands in shared memory: up to H = 105.
+bool tc_fits(int H)
 {
-    const int HP = 4 * hq, CP = col_stride(hq);
-    const size_t floats = (size_t)(HP + 2) * CP + (size_t)HP * CP + (size_t)n * MP + MP + HP + CMAX + CMAX;
-    return floats * sizeof(float);
+    const Variant *v = pick_variant(H);
+    if (!v) return false;
+    const int n = H - 1;
+    return solve_smem(v->hq, n, (n + 3) & ~3, true).total <= 220 * 1024 && tc_ndim(n) <= 256;
 }
 
 bool is_finite(double v) { return std::isfinite(v); }
@@ -858,6 +1226,10 @@ prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const flo
     p.wv = (float)w.wv; p.wa0 = (float)w.wa0; p.wa = (float)w.wa; p.wj0 = (float)w.wj0; p.wj = (float)w.wj;
     p.xi = samples; p.q0 = q0; p.v0 = v0; p.bounds = h->d_bounds;
     p.Kt = h->d_Kt32; p.kb = h->d_kb32; p.wp = h->d_wp;
+    p.Khi = h->d_Khi; p.Klo = h->d_Klo; p.err = h->d_err;
+    p.x_init = nullptr; p.dual_init = nullptr; p.dual_out = nullptr;
+    p.D = (h->mode == PRISM_MODE_ADMM) ? 4 * h->H - 1 : h->H;
+    p.polish = (h->prec == PRISM_PREC_TF32) ? 0 : iters;
     p.out = out; p.primal = nullptr; p.dual = nullptr;
     return PRISM_OK;
 }
@@ -867,9 +1239,12 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
 {
     v = pick_variant(h->H);
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", h->H);
-    fn = (h->mode == PRISM_MODE_ADMM) ? v->admm : v->paper;
-    smem = solve_smem_bytes(v->hq, h->n, h->MP);
+    const bool tc = h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32;
+    fn = (h->mode == PRISM_MODE_ADMM) ? (tc ? v->admm_tc : v->admm) : (tc ? v->paper_tc : v->paper);
+    smem = (size_t)solve_smem(v->hq, h->n, h->MP, tc).total;
     CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, (const void *)fn, NTHREADS, smem));
     if (blocks_per_sm < 1) return fail(PRISM_ERR_UNSUPPORTED, "solve kernel does not fit on an SM (smem %zu)", smem);
     const int T = std::max(1, CMAX / h->J);
@@ -984,9 +1359,13 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
     if (!(rho > 0.0) || !is_finite(rho)) return fail(PRISM_ERR_INVALID_ARG, "rho must be positive and finite");
     if (mode != PRISM_MODE_ADMM && mode != PRISM_MODE_PAPER) return fail(PRISM_ERR_INVALID_ARG, "bad mode %d", mode);
     if (scale != PRISM_SCALE_ROWNORM && scale != PRISM_SCALE_NONE) return fail(PRISM_ERR_INVALID_ARG, "bad scale %d", scale);
-    if (prec != PRISM_PREC_FP32 && prec != PRISM_PREC_BF16X3 && prec != PRISM_PREC_TF32)
+    if (prec != PRISM_PREC_FP32 && prec != PRISM_PREC_BF16X3 && prec != PRISM_PREC_TF32 &&
+        prec != PRISM_PREC_TF32X3)
         return fail(PRISM_ERR_INVALID_ARG, "bad precision %d", prec);
-    if (prec != PRISM_PREC_FP32) return fail(PRISM_ERR_UNSUPPORTED, "only PRISM_PREC_FP32 is built");
+    if (prec == PRISM_PREC_BF16X3)
+        return fail(PRISM_ERR_UNSUPPORTED, "precision %d is not built", prec);
+    if ((prec == PRISM_PREC_TF32X3 || prec == PRISM_PREC_TF32) && !tc_fits(h->H))
+        return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the tensor-core kernel limit", h->H);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int H = h->H, n = h->n, MP = h->MP;
     if (!h->d_K64) {
@@ -996,6 +1375,10 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
         CUDA_TRY(cudaMalloc(&h->d_kb32, sizeof(float) * std::max(MP, 4)));
         CUDA_TRY(cudaMalloc(&h->d_wp, sizeof(float) * PRISM_MAX_H));
         CUDA_TRY(cudaMalloc(&h->d_wfull, sizeof(double) * 4 * H));
+        CUDA_TRY(cudaMalloc(&h->d_Khi, sizeof(float) * std::max(n * n, 4)));
+        CUDA_TRY(cudaMalloc(&h->d_Klo, sizeof(float) * std::max(n * n, 4)));
+        CUDA_TRY(cudaMalloc(&h->d_err, sizeof(int)));
+        CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
     }
     const Weights w = make_weights(scale, h->dt);
     double wfull[4 * PRISM_MAX_H];
@@ -1013,7 +1396,8 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
     const size_t smem = sizeof(double) * H * H;
     CUDA_TRY(cudaFuncSetAttribute((const void *)factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const double rho_c = (mode == PRISM_MODE_PAPER ? 2.0 : 1.0) * rho;
-    factor_kernel<<<1, 256, smem, s>>>(H, rho_c, h->d_wfull, h->d_K64, h->d_kb64, h->d_Kt32, h->d_kb32, MP);
+    factor_kernel<<<1, 256, smem, s>>>(H, rho_c, h->d_wfull, h->d_K64, h->d_kb64, h->d_Kt32, h->d_kb32, MP,
+                                       h->d_Khi, h->d_Klo);
     CUDA_TRY(cudaGetLastError());
     // the host tables above are stack memory: make sure the copies completed
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -1032,6 +1416,36 @@ prism_status prism_proj_solve(prism_proj_t h, int batch, const float *q0, const 
     SolveParams p;
     prism_status st = prepare_solve(h, batch, q0, v0, samples, iters, rho, out, p);
     if (st) return st;
+    if (batch == 0) return PRISM_OK;
+    p.primal = primal_res;
+    p.dual = dual_res;
+    const Variant *v;
+    size_t smem;
+    int bps, grid;
+    solve_fn fn;
+    st = launch_config(h, batch, v, smem, bps, grid, fn);
+    if (st) return st;
+    fn<<<grid, NTHREADS, smem, (cudaStream_t)cuda_stream>>>(p);
+    CUDA_TRY(cudaGetLastError());
+    return PRISM_OK;
+}
+
+prism_status prism_proj_solve_ex(prism_proj_t h, int batch, const float *q0, const float *v0, const float *samples,
+                                 int iters, double rho, const prism_solve_opts *opts, float *out,
+                                 float *primal_res, float *dual_res, void *cuda_stream)
+{
+    SolveParams p;
+    prism_status st = prepare_solve(h, batch, q0, v0, samples, iters, rho, out, p);
+    if (st) return st;
+    if (opts) {
+        if (opts->polish_iters < 0) return fail(PRISM_ERR_INVALID_ARG, "polish_iters < 0");
+        p.x_init = opts->x_init;
+        p.dual_init = opts->dual_init;
+        p.dual_out = opts->dual_out;
+        if (h->prec == PRISM_PREC_TF32) p.polish = std::min(opts->polish_iters, iters);
+        if (batch > 0 && opts->x_init && (const void *)opts->x_init == (const void *)out)
+            return fail(PRISM_ERR_INVALID_ARG, "x_init must not alias out");
+    }
     if (batch == 0) return PRISM_OK;
     p.primal = primal_res;
     p.dual = dual_res;
@@ -1147,6 +1561,22 @@ prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_ho
     return PRISM_OK;
 }
 
+prism_status prism_proj_shift_state(prism_proj_t h, int batch, int steps, float *x, float *dual, void *cuda_stream)
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    if (!h->factored) return fail(PRISM_ERR_NOT_FACTORED, "prism_proj_factor has not been called");
+    if (batch < 0 || steps < 0) return fail(PRISM_ERR_INVALID_ARG, "batch and steps must be >= 0");
+    if (batch == 0 || steps == 0 || (!x && !dual)) return PRISM_OK;
+    const long long ncols = (long long)batch * h->J;
+    const int D = (h->mode == PRISM_MODE_ADMM) ? 4 * h->H - 1 : h->H;
+    const int tpb = 128;
+    shift_kernel<<<(unsigned)((ncols + tpb - 1) / tpb), tpb, 0, (cudaStream_t)cuda_stream>>>(
+        ncols, h->J, h->H, D, h->mode, steps, x, dual);
+    CUDA_TRY(cudaGetLastError());
+    return PRISM_OK;
+}
+
 prism_status prism_proj_check_fp64(prism_proj_t h, int batch, const float *q0, const float *v0, const float *x,
                                    double *primal_res_fp64, void *cuda_stream)
 {
@@ -1225,6 +1655,9 @@ prism_status prism_proj_destroy(prism_proj_t h)
     cudaFree(h->d_kb32);
     cudaFree(h->d_wp);
     cudaFree(h->d_wfull);
+    cudaFree(h->d_Khi);
+    cudaFree(h->d_Klo);
+    cudaFree(h->d_err);
     cudaFree(h->d_work);
     cudaFree(h->d_stage);
     delete h;

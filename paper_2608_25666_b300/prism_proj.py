@@ -19,7 +19,8 @@ import numpy as np
 
 MODE_ADMM, MODE_PAPER = 0, 1
 SCALE_ROWNORM, SCALE_NONE = 0, 1
-PREC_FP32, PREC_BF16X3, PREC_TF32 = 0, 1, 2
+PREC_FP32, PREC_BF16X3, PREC_TF32, PREC_TF32X3 = 0, 1, 2, 3
+TC_MAX_H = 105
 MAX_H, MAX_J = 132, 64
 
 STATUS = {0: "PRISM_OK", 1: "PRISM_ERR_INVALID_ARG", 2: "PRISM_ERR_NOT_FACTORED",
@@ -30,6 +31,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libprism_proj.so")
 _lock = threading.Lock()
 _lib = None
+
+
+class SolveOpts(ctypes.Structure):
+    """prism_solve_opts of the C ABI."""
+    _fields_ = [("x_init", ctypes.c_void_p), ("dual_init", ctypes.c_void_p),
+                ("dual_out", ctypes.c_void_p), ("polish_iters", ctypes.c_int)]
 
 
 class PrismError(RuntimeError):
@@ -54,12 +61,14 @@ def lib() -> ctypes.CDLL:
             L.prism_proj_solve.argtypes = sig
             L.prism_proj_solve_plain.argtypes = sig
             L.prism_proj_solve_host.argtypes = sig
+            L.prism_proj_solve_ex.argtypes = [P, i, P, P, P, i, d, P, P, P, P, P]
             L.prism_proj_check_fp64.argtypes = [P, i, P, P, P, P, P]
+            L.prism_proj_shift_state.argtypes = [P, i, i, P, P, P]
             L.prism_proj_get_factor.argtypes = [P, P, P]
             L.prism_proj_query.argtypes = [P, i, ctypes.POINTER(ll)]
             L.prism_proj_destroy.argtypes = [P]
-            for name in ("create", "factor", "solve", "solve_plain", "solve_host", "check_fp64",
-                         "get_factor", "query", "destroy"):
+            for name in ("create", "factor", "solve", "solve_ex", "solve_plain", "solve_host",
+                         "check_fp64", "shift_state", "get_factor", "query", "destroy"):
                 getattr(L, "prism_proj_" + name).restype = i
             L.prism_status_string.argtypes = [i]
             L.prism_status_string.restype = ctypes.c_char_p
@@ -156,6 +165,36 @@ class Projector:
         return self._solve(lib().prism_proj_solve, q0, v0, samples, iters, rho, out, primal, dual,
                            stream, want_res)
 
+    def dual_rows(self) -> int:
+        """Multiplier rows per column of the factored mode (4H-1 ADMM, H PAPER)."""
+        return 4 * self.H - 1 if self.mode == MODE_ADMM else self.H
+
+    def solve_ex(self, q0, v0, samples, iters: int, rho: float | None = None, x_init=None,
+                 dual_init=None, dual_out=None, polish_iters: int = 0, out=None, primal=None,
+                 dual=None, stream=None, want_res: bool = True, want_dual_out: bool = False):
+        """prism_proj_solve_ex: warm start (x_init, dual_init) and multiplier export."""
+        import torch
+        N = int(samples.shape[0])
+        D = self.dual_rows()
+        if x_init is not None:
+            _need_cuda_f32("x_init", x_init, (N, self.H, self.J))
+        if dual_init is not None:
+            _need_cuda_f32("dual_init", dual_init, (N, D, self.J))
+        if want_dual_out and dual_out is None:
+            dual_out = torch.empty((N, D, self.J), dtype=torch.float32, device=samples.device)
+        if dual_out is not None:
+            _need_cuda_f32("dual_out", dual_out, (N, D, self.J))
+        opts = SolveOpts(None if x_init is None else x_init.data_ptr(),
+                         None if dual_init is None else dual_init.data_ptr(),
+                         None if dual_out is None else dual_out.data_ptr(), int(polish_iters))
+        L = lib()
+
+        def fn(h, n, a, b_, c, it, r, o, pr, du, st):
+            return L.prism_proj_solve_ex(h, n, a, b_, c, it, r, ctypes.byref(opts), o, pr, du, st)
+
+        x, pr, du = self._solve(fn, q0, v0, samples, iters, rho, out, primal, dual, stream, want_res)
+        return x, pr, du, dual_out
+
     def solve_plain(self, q0, v0, samples, iters: int, rho: float | None = None, out=None,
                     primal=None, dual=None, stream=None, want_res: bool = True):
         """prism_proj_solve_plain (the plain FP32 comparator)."""
@@ -191,6 +230,16 @@ class Projector:
                                            float(rho), _ptr(out), _ptr(primal), _ptr(dual),
                                            _stream_ptr(stream)))
         return out, primal, dual
+
+    def shift_state(self, steps: int, x=None, dual=None, stream=None):
+        """prism_proj_shift_state: in-place receding-horizon shift of x and/or dual."""
+        N = int((x if x is not None else dual).shape[0])
+        if x is not None:
+            _need_cuda_f32("x", x, (N, self.H, self.J))
+        if dual is not None:
+            _need_cuda_f32("dual", dual, (N, self.dual_rows(), self.J))
+        _check(lib().prism_proj_shift_state(self._h, N, int(steps), _ptr(x), _ptr(dual),
+                                            _stream_ptr(stream)))
 
     def check_fp64(self, q0, v0, x, stream=None):
         """prism_proj_check_fp64: FP64 primal residual [N, J] (CUDA float64 tensor)."""

@@ -16,9 +16,13 @@ def to_dev(b):
             torch.from_numpy(b["v0"]).cuda())
 
 
-def gpu_solve(b, iters, rho=1.0, mode=pp.MODE_ADMM, scale=pp.SCALE_ROWNORM, kernel="persistent"):
+TC_MAX_H = 105       # largest horizon of the tensor-core K-apply
+
+
+def gpu_solve(b, iters, rho=1.0, mode=pp.MODE_ADMM, scale=pp.SCALE_ROWNORM, kernel="persistent",
+              prec=pp.PREC_FP32):
     import torch
-    P = pp.Projector(b["J"], b["H"], b["dt"], b["bounds"]).factor(rho, mode, scale)
+    P = pp.Projector(b["J"], b["H"], b["dt"], b["bounds"]).factor(rho, mode, scale, prec)
     xi, q0, v0 = to_dev(b)
     fn = P.solve if kernel == "persistent" else P.solve_plain
     x, pr, du = fn(q0, v0, xi, iters)
