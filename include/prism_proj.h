@@ -259,6 +259,105 @@ prism_status prism_proj_solve_plain_noalloc(prism_proj_t h, int batch, const flo
                                             double rho, float *out, float *primal_res,
                                             float *dual_res, void *cuda_stream);
 
+/*
+ * Batched plans -- many independent projection problems of differing
+ * (J, H, N, dt, bounds) in one persistent launch per kernel variant.
+ *
+ * prism_problem describes one problem: a factored handle (its J, H, dt,
+ * bounds, mode, rho and precision apply), N = batch samples and device
+ * buffers laid out as for prism_proj_solve / prism_proj_solve_ex (residual
+ * and warm-start pointers may be NULL).  The caller keeps every buffer alive
+ * and in place while the plan exists: the plan stores the pointers.
+ *
+ * prism_plan_create groups the problems by kernel variant (horizon chunk,
+ * mode, K-apply path) and uploads one descriptor table per group; a launch
+ * runs one persistent kernel per group, each over every block slot of the
+ * GPU, in sequence on the caller's stream.  flags:
+ *   PRISM_PLAN_AUTOTUNE  time each group (this runs the solves, overwriting
+ *                        the outputs) and, where all of a group's problems are
+ *                        FP32-accurate, also the other K-apply path; keep the
+ *                        faster path;
+ *   PRISM_PLAN_GRAPH     capture the launches once in a CUDA graph;
+ *                        prism_plan_launch then replays it.
+ * prism_plan_launch enqueues one execution on cuda_stream (asynchronous).
+ * prism_plan_query: group < 0 gives out[0] groups, out[1] graph (0/1),
+ *   out[2] SMs; group g gives out[0] horizon chunk, out[1] tensor cores (0/1),
+ *   out[2] problems, out[3] tiles, out[4] grid, out[5] blocks per SM, out[6]
+ *   shared memory bytes, out[7] autotune time in microseconds (-1 if none).
+ */
+typedef struct {
+    prism_proj_t h;
+    int batch;
+    const float *q0, *v0, *samples;
+    float *out, *primal_res, *dual_res;
+    const float *x_init, *dual_init;
+    float *dual_out;
+} prism_problem;
+
+typedef struct prism_plan_s *prism_plan_t;
+enum { PRISM_PLAN_AUTOTUNE = 1, PRISM_PLAN_GRAPH = 2 };
+
+prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters, int flags,
+                               prism_plan_t *out);
+prism_status prism_plan_launch(prism_plan_t plan, void *cuda_stream);
+prism_status prism_plan_query(prism_plan_t plan, int group, long long out[8]);
+prism_status prism_plan_destroy(prism_plan_t plan);
+
+/*
+ * prism_proj_describe -- shape of a handle: dims[0] J, dims[1] H, dims[2] D (multiplier
+ * rows per column: 4H-1 ADMM, H PAPER), dims[3] mode, dims[4] precision, dims[5]
+ * factored (0/1); *rho (may be NULL) the factored rho.
+ */
+prism_status prism_proj_describe(prism_proj_t h, int dims[6], double *rho);
+
+/*
+ * Serving loop -- continuous batching of projection requests from many MPC
+ * controllers (no counterpart in the paper's code; its Sec. III-B MPC loop
+ * calls the projection once per control step and warm-starts the next step).
+ *
+ * prism_server_create: a server on the current device with a device-memory
+ *   budget (one arena of mem_budget_bytes, allocated here), at most
+ *   max_inflight requests on the GPU at once (one CUDA stream each) and the
+ *   control deadline used in the statistics.  A scheduler thread admits queued
+ *   requests whenever a stream and arena memory for their buffers are free,
+ *   so newly arrived requests start while others are running.
+ * prism_server_add_controller: register a factored handle with its batch N and
+ *   iteration count; warm_start != 0 keeps the controller's multiplier on the
+ *   device between its requests (shifted one step along the horizon before
+ *   each new solve).  Admission: the controller's resident state plus one
+ *   request's buffers must fit in the remaining budget, else PRISM_ERR_OOM.
+ *   Returns the controller id.  Handles must outlive the server.
+ * prism_server_submit: queue one request (host arrays: q0, v0 [J], samples
+ *   [N][H][J], out [N][H][J], primal [N][J] or NULL).  The host arrays must
+ *   stay valid until the request finishes; pinned memory gives asynchronous
+ *   copies.  One request per controller runs at a time, in submission order; a
+ *   newer request replaces an older one that has not started (the older one is
+ *   dropped).  Returns a ticket.
+ * prism_server_wait: wait up to timeout_ms (< 0: forever) for a ticket;
+ *   *state = 0 queued, 1 running, 2 done, 3 dropped, 4 failed; *latency_ms =
+ *   submit-to-completion time (done) or -1.  A finished ticket is forgotten
+ *   after it has been waited for.
+ * prism_server_stats: out[0] completed, out[1] dropped, out[2] failed, out[3]
+ *   p50 and out[4] p99 latency (ms), out[5] max latency, out[6] deadline misses
+ *   (late or dropped), out[7] completed trajectories, out[8] trajectories/s
+ *   between the first submission and the last completion, out[9] free arena
+ *   bytes.  prism_server_reset_stats clears them.
+ * prism_server_destroy: finish in-flight work, stop the scheduler, free the arena.
+ */
+typedef struct prism_server_s *prism_server_t;
+prism_status prism_server_create(size_t mem_budget_bytes, int max_inflight, double deadline_ms,
+                                 prism_server_t *out);
+prism_status prism_server_add_controller(prism_server_t s, prism_proj_t h, int batch, int iters,
+                                         int warm_start, int *id);
+prism_status prism_server_submit(prism_server_t s, int id, const float *q0_host, const float *v0_host,
+                                 const float *samples_host, float *out_host, float *primal_host,
+                                 unsigned long long *ticket);
+prism_status prism_server_wait(prism_server_t s, unsigned long long ticket, double timeout_ms,
+                               int *state, double *latency_ms);
+prism_status prism_server_stats(prism_server_t s, double out[10]);
+prism_status prism_server_reset_stats(prism_server_t s);
+prism_status prism_server_destroy(prism_server_t s);
+
 /* prism_proj_destroy -- free the handle and its device memory (synchronises the device). */
 prism_status prism_proj_destroy(prism_proj_t h);
 

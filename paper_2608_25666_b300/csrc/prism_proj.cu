@@ -44,6 +44,9 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <map>
+#include <tuple>
+#include <vector>
 
 namespace {
 
@@ -242,9 +245,20 @@ struct SolveParams {
     float *dual_out;                     // [N][D][J] final multiplier or NULL
     int polish;                          // tensor cores: last iterations with the split K-apply
     int D;                               // multiplier rows per column: 4H-1 (ADMM) or H (PAPER)
+    int tile0;                           // first tile of this problem in a batched launch
     float *out;
     float *primal;
     float *dual;
+};
+
+// One launch of the solve kernel: a single problem (in the parameter space)
+// or a table of problems in device memory, tiles numbered problem by problem.
+struct LaunchParams {
+    SolveParams one;
+    const SolveParams *many;   // nullptr: the launch solves `one`
+    int nprob, ntiles;
+    int n_max, MP_max;         // shared-memory layout bounds over the launch's problems
+    int tmem_cols;             // tensor memory columns allocated per block
 };
 
 // Two-sided bounds of one column in the device units (computed in double,
@@ -481,6 +495,20 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8])
     for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[e]);
 }
 
+// 16 consecutive columns of this warp's lanes; columns past the allocation are
+// never requested (callers stay inside D).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+}
+
 __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 // TC operand sizes for reduced size n = H - 1.
@@ -535,16 +563,16 @@ __host__ __device__ inline SolveSmem solve_smem(int hq, int n, int MP, bool tc)
     return L;
 }
 
-template <int HQ, int MODE, bool TC>
+template <int HQ, int MODE, bool TC, bool BATCHED>
 __global__ void __launch_bounds__(NTHREADS, solve_min_blocks<HQ>())
-solve_kernel(const SolveParams p)
+solve_kernel(const __grid_constant__ LaunchParams P)
 {
     constexpr int HP = 4 * HQ;
     constexpr int CP = col_stride(HQ);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mma_bar;
-    const SolveSmem L = solve_smem(HQ, p.n, p.MP, TC);
+    const SolveSmem L = solve_smem(HQ, P.n_max, P.MP_max, TC);
     float *xs = reinterpret_cast<float *>(smem_raw + L.xs);
     float *rhs = reinterpret_cast<float *>(smem_raw + L.rhs);
     float *Kts = reinterpret_cast<float *>(smem_raw + L.kt);
@@ -559,30 +587,12 @@ solve_kernel(const SolveParams p)
     const int c = tid >> 2;       // column in tile
     const int b = tid & 3;        // time quarter
     const int i0 = b * HQ;
-    const int H = p.H, J = p.J, n = p.n;
-    const int HJ = H * J;
-    const float rho = p.rho;
-    const int KD = tc_kd(n), ND = tc_ndim(n);
 
-    // per-shape constants -> shared memory (once)
-    if (!TC)
-        for (int e = tid; e < n * p.MP; e += NTHREADS) Kts[e] = p.Kt[e];
-    for (int e = tid; e < p.MP; e += NTHREADS) kbs[e] = p.kb[e];
-    for (int e = tid; e < HP; e += NTHREADS) wps[e] = (e < H) ? p.wp[e] : 0.0f;
     uint32_t tbase = 0, mma_phase = 0;
     if (TC) {
-        // B = K' (rows i, reduction j) split in tf32 high / low parts; A zeroed
-        // once (its padding columns k >= n stay zero).
-        for (int e = tid; e < ND * KD; e += NTHREADS) {
-            const int i = e / KD, j = e - i * KD;
-            const bool in = i < n && j < n;
-            *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(i, j, KD)) = in ? p.Khi[i * n + j] : 0.0f;
-            *reinterpret_cast<float *>(smem_raw + L.blo + cm_off(i, j, KD)) = in ? p.Klo[i * n + j] : 0.0f;
-        }
-        for (int e = tid; e < 128 * KD; e += NTHREADS) reinterpret_cast<float *>(As)[e] = 0.0f;
         if (warp == 0) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                         :: "r"(smem_addr(&tmem_slot)), "r"(tc_tmem_cols(n)));
+                         :: "r"(smem_addr(&tmem_slot)), "r"(P.tmem_cols));
             asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         }
         if (tid == 0) {
@@ -595,13 +605,50 @@ solve_kernel(const SolveParams p)
         tbase = tmem_slot;
     }
     bool aborted = false;
+    int cur = -1;
 
-    for (int tile = blockIdx.x; tile < p.ntiles && !aborted; tile += gridDim.x) {
-        const int n0 = tile * p.T;
+    for (int tile = blockIdx.x; tile < P.ntiles && !aborted; tile += gridDim.x) {
+        // problem of this tile (block-uniform): binary search over first tiles
+        int pi = 0;
+        if (BATCHED) {
+            int lo = 0, hi = P.nprob - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (P.many[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+            }
+            pi = lo;
+        }
+        const SolveParams &p = BATCHED ? P.many[pi] : P.one;
+        const int H = p.H, J = p.J, n = p.n;
+        const int HJ = H * J;
+        const float rho = p.rho;
+        const float wv = p.wv, wa0 = p.wa0, wa = p.wa, wj0 = p.wj0, wj = p.wj;
+        const int iters = p.iters, polish = p.polish;
+        const int KD = tc_kd(n), ND = tc_ndim(n);
+        const int n0 = (tile - p.tile0) * p.T;
         const int Tt = min(p.T, p.N - n0);
         const int Ct = Tt * J;
         const int ncg = (Ct + 3) >> 2;
         __syncthreads();   // previous tile fully stored before xs is overwritten
+        if (pi != cur) {
+            // per-shape constants -> shared memory (once per problem change)
+            if (!TC)
+                for (int e = tid; e < n * p.MP; e += NTHREADS) Kts[e] = p.Kt[e];
+            for (int e = tid; e < p.MP; e += NTHREADS) kbs[e] = p.kb[e];
+            for (int e = tid; e < HP; e += NTHREADS) wps[e] = (e < H) ? p.wp[e] : 0.0f;
+            if (TC) {
+                // B = K' (rows i, reduction j) split in tf32 high / low parts; A
+                // zeroed (its padding columns k >= n must stay zero).
+                for (int e = tid; e < ND * KD; e += NTHREADS) {
+                    const int i = e / KD, j = e - i * KD;
+                    const bool in = i < n && j < n;
+                    *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(i, j, KD)) = in ? p.Khi[i * n + j] : 0.0f;
+                    *reinterpret_cast<float *>(smem_raw + L.blo + cm_off(i, j, KD)) = in ? p.Klo[i * n + j] : 0.0f;
+                }
+                for (int e = tid; e < 128 * KD; e += NTHREADS) reinterpret_cast<float *>(As)[e] = 0.0f;
+            }
+            cur = pi;
+        }
         // ---- a1: load the contiguous slab xi[n0 : n0+Tt][H][J] into xs rows 2..H+1
         for (int e = tid; e < (HP + 2) * CP; e += NTHREADS) xs[e] = 0.0f;
         if (tid < CMAX) {
@@ -667,13 +714,13 @@ solve_kernel(const SolveParams p)
                     const int i = i0 + r;
                     if (i < H) {
                         if (MODE == PRISM_MODE_ADMM) {
-                            t_v[r] -= __ldg(p.dual_init + base + (size_t)i * J) * rsqrtf(p.wv);
+                            t_v[r] -= __ldg(p.dual_init + base + (size_t)i * J) * rsqrtf(wv);
                             t_p[r] -= __ldg(p.dual_init + base + (size_t)(H + i) * J) * rsqrtf(wps[i]);
                             t_a[r] -= __ldg(p.dual_init + base + (size_t)(2 * H + i) * J) *
-                                      rsqrtf(i == 0 ? p.wa0 : p.wa);
+                                      rsqrtf(i == 0 ? wa0 : wa);
                             if (i >= 1)
                                 t_j[r] -= __ldg(p.dual_init + base + (size_t)(3 * H + i - 1) * J) *
-                                          rsqrtf(i == 1 ? p.wj0 : p.wj);
+                                          rsqrtf(i == 1 ? wj0 : wj);
                         } else {
                             lam[r] = __ldg(p.dual_init + base + (size_t)i * J);
                         }
@@ -682,7 +729,7 @@ solve_kernel(const SolveParams p)
             }
         }
 
-        for (int l = 0; l < p.iters; ++l) {
+        for (int l = 0; l < iters; ++l) {
             // ---- stencil phase: a3 slack / clip, a4 Fh^T, a6 multiplier -> rhs
             if (l > 0) load_xwin<HQ>(xs, CP, c, b, X);
             Rows<HQ> s;
@@ -699,18 +746,18 @@ solve_kernel(const SolveParams p)
                     float z;
                     z = clampf(2.0f * yv - t_v[r], cb.vlo, cb.vhi);
                     t_v[r] = vi ? (z - yv) + t_v[r] : 0.0f;
-                    s.v[r] = p.wv * t_v[r];
+                    s.v[r] = wv * t_v[r];
                     z = clampf(2.0f * yp - t_p[r], cb.plo, cb.phi);
                     t_p[r] = vi ? (z - yp) + t_p[r] : 0.0f;
                     s.p[r] = wps[i] * t_p[r];
                     z = (i == 0) ? clampf(2.0f * ya - t_a[r], cb.alo0, cb.ahi0)
                                  : clampf(2.0f * ya - t_a[r], cb.alo, cb.ahi);
                     t_a[r] = vi ? (z - ya) + t_a[r] : 0.0f;
-                    s.a[r] = ((i == 0) ? p.wa0 : p.wa) * t_a[r];
+                    s.a[r] = ((i == 0) ? wa0 : wa) * t_a[r];
                     z = (i == 1) ? clampf(2.0f * yj - t_j[r], cb.jlo1, cb.jhi1)
                                  : clampf(2.0f * yj - t_j[r], cb.jlo, cb.jhi);
                     t_j[r] = (vi && i >= 1) ? (z - yj) + t_j[r] : 0.0f;
-                    s.j[r] = ((i == 1) ? p.wj0 : p.wj) * t_j[r];
+                    s.j[r] = ((i == 1) ? wj0 : wj) * t_j[r];
                 }
                 apply_FT<HQ>(s, b, g);
 #pragma unroll
@@ -725,10 +772,10 @@ solve_kernel(const SolveParams p)
                         cs += X.w[r + 2];
                         const float ya = X.w[r + 2] - X.w[r + 1];
                         const float yj = ya - (X.w[r + 1] - X.w[r]);
-                        s.v[r] = vi ? p.wv * X.w[r + 2] : 0.0f;
+                        s.v[r] = vi ? wv * X.w[r + 2] : 0.0f;
                         s.p[r] = vi ? wps[i] * cs : 0.0f;
-                        s.a[r] = vi ? ((i == 0) ? p.wa0 : p.wa) * ya : 0.0f;
-                        s.j[r] = (vi && i >= 1) ? ((i == 1) ? p.wj0 : p.wj) * yj : 0.0f;
+                        s.a[r] = vi ? ((i == 0) ? wa0 : wa) * ya : 0.0f;
+                        s.j[r] = (vi && i >= 1) ? ((i == 1) ? wj0 : wj) * yj : 0.0f;
                     }
                     apply_FT<HQ>(s, b, g);
 #pragma unroll
@@ -746,10 +793,10 @@ solve_kernel(const SolveParams p)
                     const float pp = yp + clampf(yp, cb.plo, cb.phi);
                     const float pa = ya + ((i == 0) ? clampf(ya, cb.alo0, cb.ahi0) : clampf(ya, cb.alo, cb.ahi));
                     const float pj = yj + ((i == 1) ? clampf(yj, cb.jlo1, cb.jhi1) : clampf(yj, cb.jlo, cb.jhi));
-                    s.v[r] = vi ? p.wv * pv : 0.0f;
+                    s.v[r] = vi ? wv * pv : 0.0f;
                     s.p[r] = vi ? wps[i] * pp : 0.0f;
-                    s.a[r] = vi ? ((i == 0) ? p.wa0 : p.wa) * pa : 0.0f;
-                    s.j[r] = (vi && i >= 1) ? ((i == 1) ? p.wj0 : p.wj) * pj : 0.0f;
+                    s.a[r] = vi ? ((i == 0) ? wa0 : wa) * pa : 0.0f;
+                    s.j[r] = (vi && i >= 1) ? ((i == 1) ? wj0 : wj) * pj : 0.0f;
                 }
                 apply_FT<HQ>(s, b, g);
 #pragma unroll
@@ -758,7 +805,7 @@ solve_kernel(const SolveParams p)
                     lam[r] = fmaf(0.5f * rho, g[r], lam[r]);
                 }
             }
-            const bool last = (l == p.iters - 1);
+            const bool last = (l == iters - 1);
             if (!TC) {
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
@@ -770,31 +817,38 @@ solve_kernel(const SolveParams p)
                 kapply(xs, rhs, Kts, kbs, v0c, dres, n, p.MP, CP, ncg, last);
                 __syncthreads();
             } else {
-                // rhs -> A (rows c: tf32 high part, rows 64 + c: remainder), K = i - 1.
-                // Iterations before the polish phase use the high parts only.
-                const bool split = l >= p.iters - p.polish;
+                // rhs -> A_hi (tf32 high parts) and A_lo (remainders), rows = columns c,
+                // K = i - 1.  Iterations before the polish phase use the high parts only.
+                const bool split = l >= iters - polish;
+                const int a_lo = 64 * KD * 4;   // byte offset of A_lo after A_hi
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
                     const int i = i0 + r;
                     if (i >= 1 && i < H) {
                         const float hi = tf32_rna(rv[r]);
                         *reinterpret_cast<float *>(As + cm_off(c, i - 1, KD)) = hi;
-                        *reinterpret_cast<float *>(As + cm_off(CMAX + c, i - 1, KD)) = split ? rv[r] - hi : 0.0f;
+                        if (split) *reinterpret_cast<float *>(As + a_lo + cm_off(c, i - 1, KD)) = rv[r] - hi;
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();
-                // ---- a5: K-apply on the tensor cores: D[c'][i] = sum_j A[c'][j] (Khi + Klo)[i][j]
+                // ---- a5: K-apply on the tensor cores, one M=64 accumulator:
+                // D[c][i] = sum_j (A_hi Khi + A_hi Klo + A_lo Khi)[c][j][i]
                 if (tid == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t idesc = umma_idesc_tf32(128, ND);
-                    const uint32_t a0 = smem_addr(As), bh = smem_addr(smem_raw + L.bhi), bl = smem_addr(smem_raw + L.blo);
+                    const uint32_t idesc = umma_idesc_tf32(64, ND);
+                    const uint32_t ah = smem_addr(As), al = ah + (uint32_t)a_lo;
+                    const uint32_t bh = smem_addr(smem_raw + L.bhi), bl = smem_addr(smem_raw + L.blo);
                     const uint32_t sbo = (uint32_t)(KD >> 2) * 128u;
                     for (int ks = 0; ks < (KD >> 3); ++ks) {
                         const uint32_t koff = (uint32_t)ks * 256u;
-                        const uint64_t ad = umma_desc(a0 + koff, 128u, sbo);
-                        umma_tf32(tbase, ad, umma_desc(bh + koff, 128u, sbo), idesc, ks > 0 ? 1u : 0u);
-                        if (split) umma_tf32(tbase, ad, umma_desc(bl + koff, 128u, sbo), idesc, 1u);
+                        const uint64_t adh = umma_desc(ah + koff, 128u, sbo);
+                        const uint64_t bdh = umma_desc(bh + koff, 128u, sbo);
+                        umma_tf32(tbase, adh, bdh, idesc, ks > 0 ? 1u : 0u);
+                        if (split) {
+                            umma_tf32(tbase, adh, umma_desc(bl + koff, 128u, sbo), idesc, 1u);
+                            umma_tf32(tbase, umma_desc(al + koff, 128u, sbo), bdh, idesc, 1u);
+                        }
                     }
                     umma_commit(smem_addr(&mma_bar));
                 }
@@ -806,43 +860,34 @@ solve_kernel(const SolveParams p)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                // readback: warp quarter q holds TMEM lanes 32q..32q+31; lanes 0..63 are
-                // the high-part rows (column c), 64..127 the remainder rows.
-                const int q = warp & 3, half = warp >> 2;
-                const int cc = 32 * (q & 1) + lane;
-                const int NH = ND >> 1;
-                const uint32_t tl = tbase + ((uint32_t)(32 * q) << 16);
-                if (q >= 2) {
-                    for (int ch = 0; ch < NH; ch += 8) {
-                        float d[8];
-                        tmem_ld8(tl + (uint32_t)(half * NH + ch), d);
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int i = half * NH + ch + e;
-                            if (i < n) rhs[i * CP + cc] = d[e];
-                        }
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncthreads();
-                if (q < 2) {
+                // readback: with M = 64, row r of D sits in TMEM lane 32 (r / 16) + r % 16,
+                // so warp quarter q holds columns 16q .. 16q+15 in its first 16 lanes;
+                // the two warps of a quarter split the N = ND outputs in halves.
+                {
+                    const int q = warp & 3, half = warp >> 2;
+                    const int cc = 16 * q + (lane & 15);
+                    const int NH = ND >> 1;
+                    const uint32_t tl = tbase + ((uint32_t)(32 * q) << 16);
+                    const bool act = lane < 16;
                     const float v0v = v0c[cc];
                     float dm = 0.0f;
-                    for (int ch = 0; ch < NH; ch += 8) {
-                        float d[8];
-                        tmem_ld8(tl + (uint32_t)(half * NH + ch), d);
+                    for (int ch = 0; ch < NH; ch += 16) {
+                        float d[16];
+                        tmem_ld16(tl + (uint32_t)(half * NH + ch), d);
+                        if (act) {
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int i = half * NH + ch + e;
-                            if (i < n) {
-                                const float nv = fmaf(kbs[i], v0v, d[e] + rhs[i * CP + cc]);
-                                float *dst = xs + (i + 3) * CP + cc;
-                                if (last) dm = fmaxf(dm, fabsf(nv - *dst));
-                                *dst = nv;
+                            for (int e = 0; e < 16; ++e) {
+                                const int i = half * NH + ch + e;
+                                if (ch + e < NH && i < n) {
+                                    const float nv = fmaf(kbs[i], v0v, d[e]);
+                                    float *dst = xs + (i + 3) * CP + cc;
+                                    if (last) dm = fmaxf(dm, fabsf(nv - *dst));
+                                    *dst = nv;
+                                }
                             }
                         }
                     }
-                    if (last) atomicMax(&dres[cc], __float_as_uint(dm));
+                    if (last && act) atomicMax(&dres[cc], __float_as_uint(dm));
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncthreads();
@@ -888,12 +933,12 @@ solve_kernel(const SolveParams p)
                     if (colv && i < H) {
                         const float ya = X.w[r + 2] - X.w[r + 1];
                         const float yj = ya - (X.w[r + 1] - X.w[r]);
-                        p.dual_out[base + (size_t)i * J] = sqrtf(p.wv) * (X.w[r + 2] - t_v[r]);
+                        p.dual_out[base + (size_t)i * J] = sqrtf(wv) * (X.w[r + 2] - t_v[r]);
                         p.dual_out[base + (size_t)(H + i) * J] = sqrtf(wps[i]) * (cs - t_p[r]);
-                        p.dual_out[base + (size_t)(2 * H + i) * J] = sqrtf(i == 0 ? p.wa0 : p.wa) * (ya - t_a[r]);
+                        p.dual_out[base + (size_t)(2 * H + i) * J] = sqrtf(i == 0 ? wa0 : wa) * (ya - t_a[r]);
                         if (i >= 1)
                             p.dual_out[base + (size_t)(3 * H + i - 1) * J] =
-                                sqrtf(i == 1 ? p.wj0 : p.wj) * (yj - t_j[r]);
+                                sqrtf(i == 1 ? wj0 : wj) * (yj - t_j[r]);
                     }
                 }
             } else {
@@ -907,13 +952,13 @@ solve_kernel(const SolveParams p)
                     cs += X.w[r + 2];
                     const float ya = X.w[r + 2] - X.w[r + 1];
                     const float yj = ya - (X.w[r + 1] - X.w[r]);
-                    s.v[r] = vi ? p.wv * X.w[r + 2] : 0.0f;
+                    s.v[r] = vi ? wv * X.w[r + 2] : 0.0f;
                     s.p[r] = vi ? wps[i] * cs : 0.0f;
-                    s.a[r] = vi ? ((i == 0) ? p.wa0 : p.wa) * ya : 0.0f;
-                    s.j[r] = (vi && i >= 1) ? ((i == 1) ? p.wj0 : p.wj) * yj : 0.0f;
+                    s.a[r] = vi ? ((i == 0) ? wa0 : wa) * ya : 0.0f;
+                    s.j[r] = (vi && i >= 1) ? ((i == 1) ? wj0 : wj) * yj : 0.0f;
                 }
                 apply_FT<HQ>(s, b, g);
-                const bool any = p.iters > 0;
+                const bool any = iters > 0;
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
                     const int i = i0 + r;
@@ -942,7 +987,7 @@ solve_kernel(const SolveParams p)
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (warp == 0)
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(tc_tmem_cols(n)));
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(P.tmem_cols));
     }
 }
 
@@ -1159,16 +1204,19 @@ __global__ void check_kernel(int N, int J, int H, double dt, const double *__res
 // ===========================================================================
 // Host side
 // ===========================================================================
-typedef void (*solve_fn)(const SolveParams);
+typedef void (*solve_fn)(const LaunchParams);
 
 struct Variant {
     int hq;
-    solve_fn admm, paper, admm_tc, paper_tc;
+    solve_fn admm, paper, admm_tc, paper_tc;       // one problem per launch
+    solve_fn b_admm, b_paper, b_admm_tc, b_paper_tc;   // batched launches
 };
 
-#define VARIANT(HQv)                                                                              \
-    {HQv, solve_kernel<HQv, PRISM_MODE_ADMM, false>, solve_kernel<HQv, PRISM_MODE_PAPER, false>, \
-     solve_kernel<HQv, PRISM_MODE_ADMM, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true>}
+#define VARIANT(HQv)                                                                                    \
+    {HQv, solve_kernel<HQv, PRISM_MODE_ADMM, false, false>, solve_kernel<HQv, PRISM_MODE_PAPER, false, false>, \
+     solve_kernel<HQv, PRISM_MODE_ADMM, true, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false>,       \
+     solve_kernel<HQv, PRISM_MODE_ADMM, false, true>, solve_kernel<HQv, PRISM_MODE_PAPER, false, true>,       \
+     solve_kernel<HQv, PRISM_MODE_ADMM, true, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, true>}
 const Variant kVariants[] = {VARIANT(3), VARIANT(5), VARIANT(7), VARIANT(9), VARIANT(11),
                              VARIANT(13), VARIANT(15), VARIANT(17), VARIANT(21), VARIANT(25),
                              VARIANT(29), VARIANT(33)};
@@ -1229,8 +1277,51 @@ prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const flo
     p.Khi = h->d_Khi; p.Klo = h->d_Klo; p.err = h->d_err;
     p.x_init = nullptr; p.dual_init = nullptr; p.dual_out = nullptr;
     p.D = (h->mode == PRISM_MODE_ADMM) ? 4 * h->H - 1 : h->H;
+    p.tile0 = 0;
     p.polish = (h->prec == PRISM_PREC_TF32) ? 0 : iters;
     p.out = out; p.primal = nullptr; p.dual = nullptr;
+    return PRISM_OK;
+}
+
+LaunchParams single_launch(const SolveParams &p)
+{
+    LaunchParams lp;
+    lp.one = p;
+    lp.many = nullptr;
+    lp.nprob = 1;
+    lp.ntiles = p.ntiles;
+    lp.n_max = p.n;
+    lp.MP_max = p.MP;
+    lp.tmem_cols = tc_tmem_cols(p.n);
+    return lp;
+}
+
+// Kernel function, dynamic shared memory and resident blocks per SM of one
+// solve-kernel variant.
+prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, int MP_max, int device,
+                            solve_fn &fn, size_t &smem, int &blocks_per_sm, int &hq)
+{
+    const Variant *v = pick_variant(H);
+    if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", H);
+    hq = v->hq;
+    if (!batched) fn = (mode == PRISM_MODE_ADMM) ? (tc ? v->admm_tc : v->admm) : (tc ? v->paper_tc : v->paper);
+    else fn = (mode == PRISM_MODE_ADMM) ? (tc ? v->b_admm_tc : v->b_admm) : (tc ? v->b_paper_tc : v->b_paper);
+    smem = (size_t)solve_smem(v->hq, n_max, MP_max, tc).total;
+    CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, (const void *)fn, NTHREADS, smem));
+    cudaFuncAttributes fa;
+    CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)fn));
+    int smem_sm = 0, reserved = 0, regs_sm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+    CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
+    CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, device));
+    const size_t per_block = smem + fa.sharedSizeBytes + (size_t)reserved;
+    const int own = std::min(std::min((int)(smem_sm / per_block), regs_sm / std::max(1, fa.numRegs * NTHREADS)),
+                             2048 / NTHREADS);
+    blocks_per_sm = std::max(blocks_per_sm, own);
+    if (blocks_per_sm < 1) return fail(PRISM_ERR_UNSUPPORTED, "solve kernel does not fit on an SM (smem %zu)", smem);
     return PRISM_OK;
 }
 
@@ -1246,10 +1337,119 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
     CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   (int)cudaSharedmemCarveoutMaxShared));
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, (const void *)fn, NTHREADS, smem));
+    // The occupancy query under-reports for the tensor-core variant (it allows one
+    // block where the launch holds two); count registers and shared memory directly.
+    {
+        cudaFuncAttributes fa;
+        CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)fn));
+        int smem_sm = 0, reserved = 0, regs_sm = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
+        CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, h->device));
+        CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, h->device));
+        const size_t per_block = smem + fa.sharedSizeBytes + (size_t)reserved;
+        const int by_smem = (int)(smem_sm / per_block);
+        const int by_regs = regs_sm / std::max(1, fa.numRegs * NTHREADS);
+        const int own = std::min(std::min(by_smem, by_regs), 2048 / NTHREADS);
+        blocks_per_sm = std::max(blocks_per_sm, own);
+    }
     if (blocks_per_sm < 1) return fail(PRISM_ERR_UNSUPPORTED, "solve kernel does not fit on an SM (smem %zu)", smem);
     const int T = std::max(1, CMAX / h->J);
     const int ntiles = (batch + T - 1) / T;
     grid = std::min(ntiles, blocks_per_sm * h->num_sms);
+    return PRISM_OK;
+}
+
+
+// ===========================================================================
+// Batched plans: many independent problems (each with its own factored
+// handle, J, H, dt, bounds and N) solved by one persistent launch per kernel
+// variant; the launches can be captured once in a CUDA graph.
+// ===========================================================================
+struct PlanGroup {
+    int hq = 0, mode = 0;
+    bool tc = false;
+    std::vector<int> members;          // indices into the plan's problem list
+    std::vector<SolveParams> params;   // with tile0 prefix sums
+    SolveParams *d_params = nullptr;   // device copy
+    LaunchParams lp;
+    solve_fn fn = nullptr;
+    size_t smem = 0;
+    int bps = 1, grid = 1;
+    double work = 0.0;                 // relative cost estimate
+    double tuned_ms = -1.0;            // measured alone on the whole GPU (autotune)
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+}  // namespace
+
+struct prism_plan_s {
+    int device = 0, num_sms = 0, iters = 0, flags = 0;
+    std::vector<PlanGroup> groups;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// Groups run one after another on the caller's stream, each with the whole
+// GPU.  (Running them concurrently with SM shares proportional to their work
+// measured 1.7x slower on the uneven 512-problem workload: blocks of the
+// one-block-per-SM tensor-core variants could not be placed next to the
+// partially filled SMs of the others.)
+prism_status plan_enqueue(prism_plan_t pl, cudaStream_t s)
+{
+    for (PlanGroup &g : pl->groups) {
+        g.fn<<<g.grid, NTHREADS, g.smem, s>>>(g.lp);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return PRISM_OK;
+}
+
+void plan_free(prism_plan_t pl)
+{
+    if (!pl) return;
+    cudaDeviceSynchronize();
+    for (PlanGroup &g : pl->groups) {
+        cudaFree(g.d_params);
+        if (g.stream) cudaStreamDestroy(g.stream);
+        if (g.done) cudaEventDestroy(g.done);
+    }
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->fork) cudaEventDestroy(pl->fork);
+    if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
+    delete pl;
+}
+
+// Each group's persistent grid: every resident block slot of the GPU.
+void plan_size_grids(prism_plan_t pl)
+{
+    for (PlanGroup &g : pl->groups) g.grid = std::max(1, std::min(g.bps * pl->num_sms, g.lp.ntiles));
+}
+
+// Time one group alone on the whole GPU (grid = bps x SMs), best of a few runs.
+prism_status plan_time_group(prism_plan_t pl, PlanGroup &g, double &ms)
+{
+    cudaEvent_t a, b;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    const int grid = std::max(1, std::min(g.bps * pl->num_sms, g.lp.ntiles));
+    ms = 1e30;
+    for (int rep = 0; rep < 3; ++rep) {
+        CUDA_TRY(cudaEventRecord(a, g.stream));
+        g.fn<<<grid, NTHREADS, g.smem, g.stream>>>(g.lp);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaEventRecord(b, g.stream));
+        CUDA_TRY(cudaEventSynchronize(b));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+        if (rep > 0) ms = std::min(ms, (double)t);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
     return PRISM_OK;
 }
 
@@ -1305,6 +1505,19 @@ const char *prism_status_string(prism_status s)
 }
 
 const char *prism_last_error(void) { return g_last_error.c_str(); }
+
+prism_status prism_proj_describe(prism_proj_t h, int dims[6], double *rho)
+{
+    if (!h || !dims) return fail(PRISM_ERR_INVALID_ARG, "null argument");
+    dims[0] = h->J;
+    dims[1] = h->H;
+    dims[2] = (h->mode == PRISM_MODE_ADMM) ? 4 * h->H - 1 : h->H;
+    dims[3] = h->mode;
+    dims[4] = h->prec;
+    dims[5] = h->factored ? 1 : 0;
+    if (rho) *rho = h->rho;
+    return PRISM_OK;
+}
 
 prism_status prism_proj_create(int J, int H, double dt, const double *q_min, const double *q_max,
                                const double *v_min, const double *v_max, const double *a_min,
@@ -1425,7 +1638,7 @@ prism_status prism_proj_solve(prism_proj_t h, int batch, const float *q0, const 
     solve_fn fn;
     st = launch_config(h, batch, v, smem, bps, grid, fn);
     if (st) return st;
-    fn<<<grid, NTHREADS, smem, (cudaStream_t)cuda_stream>>>(p);
+    fn<<<grid, NTHREADS, smem, (cudaStream_t)cuda_stream>>>(single_launch(p));
     CUDA_TRY(cudaGetLastError());
     return PRISM_OK;
 }
@@ -1455,7 +1668,7 @@ prism_status prism_proj_solve_ex(prism_proj_t h, int batch, const float *q0, con
     solve_fn fn;
     st = launch_config(h, batch, v, smem, bps, grid, fn);
     if (st) return st;
-    fn<<<grid, NTHREADS, smem, (cudaStream_t)cuda_stream>>>(p);
+    fn<<<grid, NTHREADS, smem, (cudaStream_t)cuda_stream>>>(single_launch(p));
     CUDA_TRY(cudaGetLastError());
     return PRISM_OK;
 }
@@ -1644,6 +1857,212 @@ prism_status prism_proj_query(prism_proj_t h, int batch, long long out[8])
     return PRISM_OK;
 }
 
+prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters, int flags, prism_plan_t *out)
+{
+    if (!out) return fail(PRISM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!probs || nprob < 1) return fail(PRISM_ERR_INVALID_ARG, "no problems");
+    if (iters < 0) return fail(PRISM_ERR_INVALID_ARG, "iters < 0");
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    prism_plan_t pl = new (std::nothrow) prism_plan_s;
+    if (!pl) return fail(PRISM_ERR_OOM, "host allocation failed");
+    pl->device = dev;
+    pl->iters = iters;
+    pl->flags = flags;
+    prism_status st = PRISM_OK;
+    std::map<std::tuple<int, int, int>, int> index;   // (hq, mode, tc) -> group
+    std::vector<SolveParams> all(nprob);
+    std::vector<bool> use_tc(nprob);
+    for (int k = 0; k < nprob && !st; ++k) {
+        const prism_problem &q = probs[k];
+        if (!q.h) { st = fail(PRISM_ERR_INVALID_ARG, "problem %d: null handle", k); break; }
+        st = prepare_solve(q.h, q.batch, q.q0, q.v0, q.samples, iters, q.h->rho, q.out, all[k]);
+        if (st) break;
+        if (q.h->device != dev) { st = fail(PRISM_ERR_INVALID_ARG, "problem %d: handle on another device", k); break; }
+        all[k].primal = q.primal_res;
+        all[k].dual = q.dual_res;
+        all[k].x_init = q.x_init;
+        all[k].dual_init = q.dual_init;
+        all[k].dual_out = q.dual_out;
+        pl->num_sms = q.h->num_sms;
+        use_tc[k] = q.h->prec == PRISM_PREC_TF32X3 || q.h->prec == PRISM_PREC_TF32;
+        const Variant *v = pick_variant(q.h->H);
+        if (!v) { st = fail(PRISM_ERR_UNSUPPORTED, "problem %d: H too large", k); break; }
+        const auto key = std::make_tuple(v->hq, q.h->mode, (int)use_tc[k]);
+        auto it = index.find(key);
+        int gi;
+        if (it == index.end()) {
+            gi = (int)pl->groups.size();
+            index[key] = gi;
+            pl->groups.emplace_back();
+            pl->groups[gi].hq = v->hq;
+            pl->groups[gi].mode = q.h->mode;
+            pl->groups[gi].tc = use_tc[k];
+        } else {
+            gi = it->second;
+        }
+        pl->groups[gi].members.push_back(k);
+    }
+    if (!st) {
+        for (PlanGroup &g : pl->groups) {
+            int tiles = 0, n_max = 1, MP_max = 4, Hmax = 2;
+            for (int k : g.members) {
+                SolveParams sp = all[k];
+                if (sp.N == 0) continue;   // empty problems contribute no tiles
+                sp.tile0 = tiles;
+                tiles += sp.ntiles;
+                n_max = std::max(n_max, sp.n);
+                MP_max = std::max(MP_max, sp.MP);
+                Hmax = std::max(Hmax, sp.H);
+                g.work += (double)sp.N * sp.J * (2.0 * (sp.H - 1) * (sp.H - 1) + 43.0 * sp.H);
+                g.params.push_back(sp);
+            }
+            g.lp.one = g.params.empty() ? all[g.members[0]] : g.params[0];
+            g.lp.many = nullptr;
+            g.lp.nprob = (int)g.params.size();
+            g.lp.ntiles = tiles;
+            g.lp.n_max = n_max;
+            g.lp.MP_max = MP_max;
+            g.lp.tmem_cols = tc_tmem_cols(n_max);
+            int hq;
+            st = variant_config(Hmax, g.mode, g.tc, true, n_max, MP_max, dev, g.fn, g.smem, g.bps, hq);
+            if (st) break;
+            if (!g.params.empty()) {
+                cudaError_t e = cudaMalloc(&g.d_params, sizeof(SolveParams) * g.params.size());
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(g.d_params, g.params.data(), sizeof(SolveParams) * g.params.size(),
+                                   cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) { st = fail(PRISM_ERR_CUDA, "plan descriptors: %s", cudaGetErrorString(e)); break; }
+            }
+            g.lp.many = g.d_params;
+            cudaError_t e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+            if (e != cudaSuccess) { st = fail(PRISM_ERR_CUDA, "plan streams: %s", cudaGetErrorString(e)); break; }
+        }
+        // drop groups without tiles (all of their problems are empty)
+        std::vector<PlanGroup> keep;
+        for (PlanGroup &g : pl->groups) {
+            if (g.lp.ntiles > 0) keep.push_back(g);
+            else {
+                cudaFree(g.d_params);
+                if (g.stream) cudaStreamDestroy(g.stream);
+                if (g.done) cudaEventDestroy(g.done);
+            }
+        }
+        pl->groups.swap(keep);
+    }
+    if (!st) {
+        cudaError_t e = cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) st = fail(PRISM_ERR_CUDA, "plan event: %s", cudaGetErrorString(e));
+    }
+    if (!st && (flags & PRISM_PLAN_AUTOTUNE)) {
+        // measure each group alone; for groups whose problems are all FP32-accurate
+        // (FP32 or split TF32) also try the other K-apply and keep the faster one
+        for (PlanGroup &g : pl->groups) {
+            if (st) break;
+            double ms = 0.0;
+            st = plan_time_group(pl, g, ms);
+            if (st) break;
+            bool can_switch = true;
+            for (int k : g.members) {
+                const int prec = probs[k].h->prec;
+                if (prec == PRISM_PREC_TF32 || (!g.tc && !tc_fits(probs[k].h->H))) can_switch = false;
+            }
+            if (can_switch) {
+                PlanGroup alt = g;
+                alt.tc = !g.tc;
+                if (alt.tc) alt.lp.tmem_cols = tc_tmem_cols(alt.lp.n_max);
+                int hq;
+                int Hmax = 2;
+                for (int k : g.members) Hmax = std::max(Hmax, probs[k].h->H);
+                st = variant_config(Hmax, alt.mode, alt.tc, true, alt.lp.n_max, alt.lp.MP_max, dev, alt.fn, alt.smem,
+                                    alt.bps, hq);
+                if (st) break;
+                double ms2 = 0.0;
+                st = plan_time_group(pl, alt, ms2);
+                if (st) break;
+                if (ms2 < ms) {
+                    g.tc = alt.tc; g.fn = alt.fn; g.smem = alt.smem; g.bps = alt.bps; g.lp = alt.lp;
+                    ms = ms2;
+                }
+            }
+            g.tuned_ms = ms;
+        }
+        if (!st) {
+            int err = 0;
+            cudaMemcpy(&err, probs[0].h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+            if (err) st = fail(PRISM_ERR_CUDA, "tensor-core wait timed out during autotuning");
+        }
+    }
+    if (!st) plan_size_grids(pl);
+    if (!st && (flags & PRISM_PLAN_GRAPH)) {
+        cudaError_t e = cudaStreamCreateWithFlags(&pl->capture_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(pl->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) st = fail(PRISM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        if (!st) {
+            prism_status st2 = plan_enqueue(pl, pl->capture_stream);
+            e = cudaStreamEndCapture(pl->capture_stream, &pl->graph);
+            if (st2) st = st2;
+            else if (e != cudaSuccess) st = fail(PRISM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        if (!st) {
+            e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+            if (e != cudaSuccess) st = fail(PRISM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    if (st) {
+        plan_free(pl);
+        return st;
+    }
+    *out = pl;
+    return PRISM_OK;
+}
+
+prism_status prism_plan_launch(prism_plan_t pl, void *cuda_stream)
+{
+    if (!pl) return fail(PRISM_ERR_INVALID_ARG, "null plan");
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != pl->device) return fail(PRISM_ERR_INVALID_ARG, "current device differs from the plan's device");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (pl->exec) {
+        CUDA_TRY(cudaGraphLaunch(pl->exec, s));
+        return PRISM_OK;
+    }
+    return plan_enqueue(pl, s);
+}
+
+prism_status prism_plan_query(prism_plan_t pl, int group, long long out[8])
+{
+    if (!pl || !out) return fail(PRISM_ERR_INVALID_ARG, "null argument");
+    if (group < 0) {
+        out[0] = (long long)pl->groups.size();
+        out[1] = pl->exec ? 1 : 0;
+        out[2] = pl->num_sms;
+        for (int k = 3; k < 8; ++k) out[k] = 0;
+        return PRISM_OK;
+    }
+    if (group >= (int)pl->groups.size()) return fail(PRISM_ERR_INVALID_ARG, "group %d out of range", group);
+    const PlanGroup &g = pl->groups[group];
+    out[0] = g.hq;
+    out[1] = g.tc ? 1 : 0;
+    out[2] = g.lp.nprob;
+    out[3] = g.lp.ntiles;
+    out[4] = g.grid;
+    out[5] = g.bps;
+    out[6] = (long long)g.smem;
+    out[7] = g.tuned_ms > 0 ? (long long)std::llround(g.tuned_ms * 1000.0) : -1;
+    return PRISM_OK;
+}
+
+prism_status prism_plan_destroy(prism_plan_t pl)
+{
+    if (!pl) return fail(PRISM_ERR_INVALID_ARG, "null plan");
+    plan_free(pl);
+    return PRISM_OK;
+}
+
 prism_status prism_proj_destroy(prism_proj_t h)
 {
     if (!h) return fail(PRISM_ERR_INVALID_ARG, "null handle");
@@ -1665,3 +2084,9 @@ prism_status prism_proj_destroy(prism_proj_t h)
 }
 
 }  // extern "C"
+
+// Shared with the serving loop (prism_server.cpp); not part of the C ABI.
+__attribute__((visibility("hidden"))) prism_status prism_internal_fail(prism_status s, const char *msg)
+{
+    return fail(s, "%s", msg);
+}

@@ -39,6 +39,17 @@ class SolveOpts(ctypes.Structure):
                 ("dual_out", ctypes.c_void_p), ("polish_iters", ctypes.c_int)]
 
 
+class Problem(ctypes.Structure):
+    """prism_problem of the C ABI."""
+    _fields_ = [("h", ctypes.c_void_p), ("batch", ctypes.c_int),
+                ("q0", ctypes.c_void_p), ("v0", ctypes.c_void_p), ("samples", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("primal_res", ctypes.c_void_p), ("dual_res", ctypes.c_void_p),
+                ("x_init", ctypes.c_void_p), ("dual_init", ctypes.c_void_p), ("dual_out", ctypes.c_void_p)]
+
+
+PLAN_AUTOTUNE, PLAN_GRAPH = 1, 2
+
+
 class PrismError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -70,6 +81,25 @@ def lib() -> ctypes.CDLL:
             for name in ("create", "factor", "solve", "solve_ex", "solve_plain", "solve_host",
                          "check_fp64", "shift_state", "get_factor", "query", "destroy"):
                 getattr(L, "prism_proj_" + name).restype = i
+            L.prism_plan_create.argtypes = [P, i, i, i, ctypes.POINTER(P)]
+            L.prism_plan_launch.argtypes = [P, P]
+            L.prism_plan_query.argtypes = [P, i, ctypes.POINTER(ll)]
+            L.prism_plan_destroy.argtypes = [P]
+            for name in ("create", "launch", "query", "destroy"):
+                getattr(L, "prism_plan_" + name).restype = i
+            L.prism_proj_describe.argtypes = [P, P, P]
+            L.prism_proj_describe.restype = i
+            sz = ctypes.c_size_t
+            L.prism_server_create.argtypes = [sz, i, d, ctypes.POINTER(P)]
+            L.prism_server_add_controller.argtypes = [P, P, i, i, i, ctypes.POINTER(i)]
+            L.prism_server_submit.argtypes = [P, i, P, P, P, P, P, ctypes.POINTER(ctypes.c_ulonglong)]
+            L.prism_server_wait.argtypes = [P, ctypes.c_ulonglong, d, ctypes.POINTER(i),
+                                            ctypes.POINTER(d)]
+            L.prism_server_stats.argtypes = [P, P]
+            L.prism_server_reset_stats.argtypes = [P]
+            L.prism_server_destroy.argtypes = [P]
+            for name in ("create", "add_controller", "submit", "wait", "stats", "reset_stats", "destroy"):
+                getattr(L, "prism_server_" + name).restype = i
             L.prism_status_string.argtypes = [i]
             L.prism_status_string.restype = ctypes.c_char_p
             L.prism_last_error.argtypes = []
@@ -281,3 +311,125 @@ class Projector:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Plan:
+    """prism_plan_*: many uneven problems solved by concurrent persistent launches.
+
+    ``items`` is a list of dicts with keys proj (a factored Projector), q0, v0,
+    samples, out and optionally primal, dual, x_init, dual_init, dual_out (CUDA
+    float32 tensors in the single-solve layouts).  The tensors must stay alive
+    and in place while the plan exists.
+    """
+
+    def __init__(self, items, iters: int, autotune: bool = False, graph: bool = False):
+        self._keep = items
+        arr = (Problem * len(items))()
+        for k, it in enumerate(items):
+            P = it["proj"]
+            N = int(it["samples"].shape[0])
+            arr[k].h = P._h.value
+            arr[k].batch = N
+            for name in ("q0", "v0", "samples", "out", "primal", "dual", "x_init", "dual_init",
+                         "dual_out"):
+                t = it.get(name)
+                field = {"primal": "primal_res", "dual": "dual_res"}.get(name, name)
+                setattr(arr[k], field, None if t is None else t.data_ptr())
+        self._arr = arr
+        flags = (PLAN_AUTOTUNE if autotune else 0) | (PLAN_GRAPH if graph else 0)
+        h = ctypes.c_void_p()
+        _check(lib().prism_plan_create(ctypes.cast(arr, ctypes.c_void_p), len(items), int(iters), flags,
+                                       ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().prism_plan_launch(self._h, _stream_ptr(stream)))
+
+    def query(self):
+        out = (ctypes.c_longlong * 8)()
+        _check(lib().prism_plan_query(self._h, -1, out))
+        info = {"groups": [], "graph": bool(out[1]), "num_sms": int(out[2])}
+        for g in range(int(out[0])):
+            o = (ctypes.c_longlong * 8)()
+            _check(lib().prism_plan_query(self._h, g, o))
+            info["groups"].append(dict(zip(("hq", "tensor_cores", "problems", "tiles", "grid",
+                                            "blocks_per_sm", "smem_bytes", "autotune_us"),
+                                           [int(v) for v in o])))
+        return info
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(lib().prism_plan_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+REQUEST_STATES = {0: "queued", 1: "running", 2: "done", 3: "dropped", 4: "failed"}
+
+
+class Server:
+    """prism_server_*: continuous-batching request loop over many controllers.
+
+    Host arrays passed to ``submit`` (numpy float32 or pinned CPU tensors) are
+    kept referenced here until their ticket has been waited for.
+    """
+
+    def __init__(self, mem_budget_bytes: int = 8 << 30, max_inflight: int = 16,
+                 deadline_ms: float = 20.0):
+        h = ctypes.c_void_p()
+        _check(lib().prism_server_create(int(mem_budget_bytes), int(max_inflight), float(deadline_ms),
+                                         ctypes.byref(h)))
+        self._h = h
+        self._refs = {}
+        self._projs = []
+
+    def add_controller(self, proj: Projector, batch: int, iters: int, warm: bool = True) -> int:
+        cid = ctypes.c_int()
+        _check(lib().prism_server_add_controller(self._h, proj._h, int(batch), int(iters), int(bool(warm)),
+                                                 ctypes.byref(cid)))
+        self._projs.append(proj)
+        return int(cid.value)
+
+    def submit(self, cid: int, q0, v0, samples, out, primal=None) -> int:
+        t = ctypes.c_ulonglong()
+        _check(lib().prism_server_submit(self._h, int(cid), _ptr(q0), _ptr(v0), _ptr(samples), _ptr(out),
+                                         _ptr(primal), ctypes.byref(t)))
+        self._refs[int(t.value)] = (q0, v0, samples, out, primal)
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0):
+        st = ctypes.c_int()
+        lat = ctypes.c_double()
+        _check(lib().prism_server_wait(self._h, int(ticket), float(timeout_ms), ctypes.byref(st),
+                                       ctypes.byref(lat)))
+        state = REQUEST_STATES.get(int(st.value), int(st.value))
+        if state in ("done", "dropped", "failed"):
+            self._refs.pop(int(ticket), None)
+        return state, float(lat.value)
+
+    def stats(self) -> dict:
+        out = (ctypes.c_double * 10)()
+        _check(lib().prism_server_stats(self._h, ctypes.cast(out, ctypes.c_void_p)))
+        keys = ("completed", "dropped", "failed", "p50_ms", "p99_ms", "max_ms", "deadline_misses",
+                "trajectories", "trajectories_per_s", "free_bytes")
+        return dict(zip(keys, [float(v) for v in out]))
+
+    def reset_stats(self):
+        _check(lib().prism_server_reset_stats(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(lib().prism_server_destroy(self._h))
+            self._h = None
+            self._refs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
