@@ -556,7 +556,7 @@ __host__ __device__ inline SolveSmem solve_smem(int hq, int n, int MP, bool tc)
     L.rhs = off; off += HP * CP * 4;          // SIMT: rhs; tensor cores: lower-half partial sums
     L.kt = off;  off += tc ? 0 : n * MP * 4;
     L.kb = off;  off += MP * 4;
-    L.wp = off;  off += HP * 4;
+    L.wp = off;  off += 4 * HP * 4;        // per-row weights: position, velocity, acceleration, jerk
     L.v0c = off; off += CMAX * 4;
     L.dres = off; off += CMAX * 4;
     L.total = off;
@@ -577,7 +577,12 @@ solve_kernel(const __grid_constant__ LaunchParams P)
     float *rhs = reinterpret_cast<float *>(smem_raw + L.rhs);
     float *Kts = reinterpret_cast<float *>(smem_raw + L.kt);
     float *kbs = reinterpret_cast<float *>(smem_raw + L.kb);
+    // Per-row weight tables indexed by time: zero on rows that do not exist
+    // (jerk row 0, padding rows i >= H), so those rows never reach F^T.
     float *wps = reinterpret_cast<float *>(smem_raw + L.wp);
+    float *wvs = wps + HP;
+    float *was = wvs + HP;
+    float *wjs = was + HP;
     float *v0c = reinterpret_cast<float *>(smem_raw + L.v0c);
     unsigned *dres = reinterpret_cast<unsigned *>(smem_raw + L.dres);
     unsigned char *As = smem_raw + L.a;
@@ -635,7 +640,12 @@ solve_kernel(const __grid_constant__ LaunchParams P)
             if (!TC)
                 for (int e = tid; e < n * p.MP; e += NTHREADS) Kts[e] = p.Kt[e];
             for (int e = tid; e < p.MP; e += NTHREADS) kbs[e] = p.kb[e];
-            for (int e = tid; e < HP; e += NTHREADS) wps[e] = (e < H) ? p.wp[e] : 0.0f;
+            for (int e = tid; e < HP; e += NTHREADS) {
+                wps[e] = (e < H) ? p.wp[e] : 0.0f;
+                wvs[e] = (e < H) ? p.wv : 0.0f;
+                was[e] = (e < H) ? (e == 0 ? p.wa0 : p.wa) : 0.0f;
+                wjs[e] = (e >= 1 && e < H) ? (e == 1 ? p.wj0 : p.wj) : 0.0f;
+            }
             if (TC) {
                 // B = K' (rows i, reduction j) split in tf32 high / low parts; A
                 // zeroed (its padding columns k >= n must stay zero).
@@ -734,30 +744,34 @@ solve_kernel(const __grid_constant__ LaunchParams P)
             if (l > 0) load_xwin<HQ>(xs, CP, c, b, X);
             Rows<HQ> s;
             float g[HQ], rv[HQ];
+            // Rows that do not exist carry zero weight, so their multiplier state may
+            // drift freely (it stays finite: the drift per iteration is bounded by
+            // the row's own violation) without reaching the iterate.  The acceleration
+            // row k=1 and the first jerk row (k=2) have shifted bounds; they only
+            // occur in quarter 0 at r = 0 and r = 1, so the test is compile-time for r >= 2.
             if (MODE == PRISM_MODE_ADMM) {
                 float cs = X.pre;
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
                     const int i = i0 + r;
-                    const bool vi = colv && i < H;
+                    const bool f0 = (r == 0) && (b == 0);
+                    const bool f1 = (r == 1) && (b == 0);
                     cs += X.w[r + 2];
                     const float yv = X.w[r + 2], yp = cs, ya = X.w[r + 2] - X.w[r + 1];
                     const float yj = ya - (X.w[r + 1] - X.w[r]);
                     float z;
                     z = clampf(2.0f * yv - t_v[r], cb.vlo, cb.vhi);
-                    t_v[r] = vi ? (z - yv) + t_v[r] : 0.0f;
-                    s.v[r] = wv * t_v[r];
+                    t_v[r] = (z - yv) + t_v[r];
+                    s.v[r] = wvs[i] * t_v[r];
                     z = clampf(2.0f * yp - t_p[r], cb.plo, cb.phi);
-                    t_p[r] = vi ? (z - yp) + t_p[r] : 0.0f;
+                    t_p[r] = (z - yp) + t_p[r];
                     s.p[r] = wps[i] * t_p[r];
-                    z = (i == 0) ? clampf(2.0f * ya - t_a[r], cb.alo0, cb.ahi0)
-                                 : clampf(2.0f * ya - t_a[r], cb.alo, cb.ahi);
-                    t_a[r] = vi ? (z - ya) + t_a[r] : 0.0f;
-                    s.a[r] = ((i == 0) ? wa0 : wa) * t_a[r];
-                    z = (i == 1) ? clampf(2.0f * yj - t_j[r], cb.jlo1, cb.jhi1)
-                                 : clampf(2.0f * yj - t_j[r], cb.jlo, cb.jhi);
-                    t_j[r] = (vi && i >= 1) ? (z - yj) + t_j[r] : 0.0f;
-                    s.j[r] = ((i == 1) ? wj0 : wj) * t_j[r];
+                    z = f0 ? clampf(2.0f * ya - t_a[r], cb.alo0, cb.ahi0) : clampf(2.0f * ya - t_a[r], cb.alo, cb.ahi);
+                    t_a[r] = (z - ya) + t_a[r];
+                    s.a[r] = was[i] * t_a[r];
+                    z = f1 ? clampf(2.0f * yj - t_j[r], cb.jlo1, cb.jhi1) : clampf(2.0f * yj - t_j[r], cb.jlo, cb.jhi);
+                    t_j[r] = (z - yj) + t_j[r];
+                    s.j[r] = wjs[i] * t_j[r];
                 }
                 apply_FT<HQ>(s, b, g);
 #pragma unroll
@@ -768,14 +782,13 @@ solve_kernel(const __grid_constant__ LaunchParams P)
 #pragma unroll
                     for (int r = 0; r < HQ; ++r) {
                         const int i = i0 + r;
-                        const bool vi = colv && i < H;
                         cs += X.w[r + 2];
                         const float ya = X.w[r + 2] - X.w[r + 1];
                         const float yj = ya - (X.w[r + 1] - X.w[r]);
-                        s.v[r] = vi ? wv * X.w[r + 2] : 0.0f;
-                        s.p[r] = vi ? wps[i] * cs : 0.0f;
-                        s.a[r] = vi ? ((i == 0) ? wa0 : wa) * ya : 0.0f;
-                        s.j[r] = (vi && i >= 1) ? ((i == 1) ? wj0 : wj) * yj : 0.0f;
+                        s.v[r] = wvs[i] * X.w[r + 2];
+                        s.p[r] = wps[i] * cs;
+                        s.a[r] = was[i] * ya;
+                        s.j[r] = wjs[i] * yj;
                     }
                     apply_FT<HQ>(s, b, g);
 #pragma unroll
@@ -785,18 +798,19 @@ solve_kernel(const __grid_constant__ LaunchParams P)
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
                     const int i = i0 + r;
-                    const bool vi = colv && i < H;
+                    const bool f0 = (r == 0) && (b == 0);
+                    const bool f1 = (r == 1) && (b == 0);
                     cs += X.w[r + 2];
                     const float yv = X.w[r + 2], yp = cs, ya = X.w[r + 2] - X.w[r + 1];
                     const float yj = ya - (X.w[r + 1] - X.w[r]);
                     const float pv = yv + clampf(yv, cb.vlo, cb.vhi);
                     const float pp = yp + clampf(yp, cb.plo, cb.phi);
-                    const float pa = ya + ((i == 0) ? clampf(ya, cb.alo0, cb.ahi0) : clampf(ya, cb.alo, cb.ahi));
-                    const float pj = yj + ((i == 1) ? clampf(yj, cb.jlo1, cb.jhi1) : clampf(yj, cb.jlo, cb.jhi));
-                    s.v[r] = vi ? wv * pv : 0.0f;
-                    s.p[r] = vi ? wps[i] * pp : 0.0f;
-                    s.a[r] = vi ? ((i == 0) ? wa0 : wa) * pa : 0.0f;
-                    s.j[r] = (vi && i >= 1) ? ((i == 1) ? wj0 : wj) * pj : 0.0f;
+                    const float pa = ya + (f0 ? clampf(ya, cb.alo0, cb.ahi0) : clampf(ya, cb.alo, cb.ahi));
+                    const float pj = yj + (f1 ? clampf(yj, cb.jlo1, cb.jhi1) : clampf(yj, cb.jlo, cb.jhi));
+                    s.v[r] = wvs[i] * pv;
+                    s.p[r] = wps[i] * pp;
+                    s.a[r] = was[i] * pa;
+                    s.j[r] = wjs[i] * pj;
                 }
                 apply_FT<HQ>(s, b, g);
 #pragma unroll
@@ -807,11 +821,10 @@ solve_kernel(const __grid_constant__ LaunchParams P)
             }
             const bool last = (l == iters - 1);
             if (!TC) {
+                // every thread owns rows i0..i0+HQ-1 < 4*HQ of rhs; rows 0 and >= H are
+                // never read by the K-apply, so the stores need no guard
 #pragma unroll
-                for (int r = 0; r < HQ; ++r) {
-                    const int i = i0 + r;
-                    if (i >= 1 && i < H) rhs[i * CP + c] = rv[r];
-                }
+                for (int r = 0; r < HQ; ++r) rhs[(i0 + r) * CP + c] = rv[r];
                 __syncthreads();
                 // ---- a5: K-apply on the FP32 pipe
                 kapply(xs, rhs, Kts, kbs, v0c, dres, n, p.MP, CP, ncg, last);
