@@ -167,6 +167,26 @@ prism_status prism_proj_solve_ex(prism_proj_t h, int batch, const float *q0, con
                                  float *dual_res, void *cuda_stream);
 
 /*
+ * prism_proj_sample_solve -- draw the batch on the device and project it: the
+ * sampling step of Alg. 1 (xi ~ N(nu, diag(std^2))) fused into the solve, so
+ * the samples never travel through HBM as an input.
+ *   mean, std  device float [H][J]: nu and the per-entry standard deviation
+ *   seed, stream_id  generator key and stream: xi[n][k][j] = mean[k][j] +
+ *              std[k][j] * z_e with e = (n*H + k)*J + j; z_e is output e % 4 of
+ *              Philox4x32-10 (Salmon et al., SC 2011) at counter (e/4 low, e/4
+ *              high, stream_id low, stream_id high), key (seed low, seed high),
+ *              through the Box-Muller transform on the word pairs (0,1), (2,3)
+ *              with u = (w + 0.5) / 2^32.  Use a new stream_id per draw.
+ *   samples_out  device float [N][H][J] receives the drawn xi, or NULL
+ *   Other arguments and results as prism_proj_solve.
+ */
+prism_status prism_proj_sample_solve(prism_proj_t h, int batch, const float *q0, const float *v0,
+                                     const float *mean, const float *std, unsigned long long seed,
+                                     unsigned long long stream_id, int iters, double rho, float *out,
+                                     float *samples_out, float *primal_res, float *dual_res,
+                                     void *cuda_stream);
+
+/*
  * prism_proj_solve_plain -- the same projection computed by the plain FP32
  * comparator: one thread per column, the iteration state in a device
  * workspace that the handle allocates on first use (and grows), the cached
@@ -357,6 +377,23 @@ prism_status prism_server_wait(prism_server_t s, unsigned long long ticket, doub
 prism_status prism_server_stats(prism_server_t s, double out[10]);
 prism_status prism_server_reset_stats(prism_server_t s);
 prism_status prism_server_destroy(prism_server_t s);
+
+/*
+ * Distribution update around the projection (paper Alg. 1, Eqs. weight_update,
+ * mean_update_new, cov_update_new): from per-sample costs c [N] and projected
+ * trajectories x [N][H][J] (device),
+ *   w_n = exp(-c_n / temperature) / sum_m exp(-c_m / temperature)
+ *   mean[k][j] = sum_n w_n x[n][k][j]
+ *   var[k][j]  = sum_n w_n (x[n][k][j] - mean[k][j])^2 + eps
+ * (the diagonal covariance).  mean and var are device [H][J]; weights (device
+ * [N], may be NULL) receives w.  The caller passes a device workspace of at
+ * least prism_mppi_workspace_bytes(N, H, J) bytes; nothing is allocated.
+ * FP32 with a fixed reduction order (deterministic); enqueued on cuda_stream.
+ */
+size_t prism_mppi_workspace_bytes(int N, int H, int J);
+prism_status prism_mppi_update(int N, int H, int J, const float *cost, double temperature, double eps,
+                               const float *x, float *mean, float *var, float *weights, void *workspace,
+                               size_t workspace_bytes, void *cuda_stream);
 
 /* prism_proj_destroy -- free the handle and its device memory (synchronises the device). */
 prism_status prism_proj_destroy(prism_proj_t h);

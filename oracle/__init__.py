@@ -54,6 +54,10 @@ def _load():
             lib.oracle_solve_batch.restype = i
             lib.oracle_exact_projection.argtypes = [i, d, P, d, d, P, d, d, ll, P, P]
             lib.oracle_exact_projection.restype = ll
+            lib.oracle_philox4x32_10.argtypes = [P, P, P]
+            lib.oracle_philox4x32_10.restype = None
+            lib.oracle_sample_batch.argtypes = [i, i, i, P, P, ctypes.c_ulonglong, ctypes.c_ulonglong, P]
+            lib.oracle_sample_batch.restype = i
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = i
             _lib = lib
@@ -146,3 +150,25 @@ def exact_projection(xi_col, H: int, dt: float, bnd, q0: float, v0: float,
     if it < 0:
         raise ValueError("oracle_exact_projection failed")
     return x, int(it), float(viol[0])
+
+
+def philox4x32_10(counter, key):
+    """Philox4x32-10 block: four uint32 words from a 4-word counter and a 2-word key."""
+    lib = _load()
+    c = np.ascontiguousarray(np.asarray(counter, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    lib.oracle_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def sample_batch(N, H, J, mean, std, seed: int, stream: int):
+    """xi [N][H][J] = mean + std * z, z from Philox4x32-10 + Box-Muller (see prism_oracle.c)."""
+    lib = _load()
+    m = _f64(mean).reshape(H, J)
+    sd = _f64(std).reshape(H, J)
+    xi = np.zeros((N, H, J))
+    rc = lib.oracle_sample_batch(int(N), int(H), int(J), _p(m), _p(sd), int(seed), int(stream), _p(xi))
+    if rc:
+        raise ValueError("oracle_sample_batch failed")
+    return xi

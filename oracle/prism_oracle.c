@@ -542,3 +542,73 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------------------
+ * Sampling of Alg. 1 ("Draw a batch of n velocity-sequence samples from
+ * N(nu, Sigma)", diagonal Sigma): xi[n][k][j] = mean[k][j] + std[k][j] * z with
+ * z standard normal.  The normals come from the counter-based generator
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC 2011) and the Box-Muller transform, so that any element can
+ * be drawn independently:
+ *   element e = (n*H + k)*J + j;  block q = e / 4;  counter = (q_lo, q_hi,
+ *   stream_lo, stream_hi), key = (seed_lo, seed_hi);  the block's four words
+ *   w0..w3 give u = (w + 0.5) / 2^32 and the pairs (w0,w1), (w2,w3) give
+ *   z = sqrt(-2 ln u_a) * (cos(2 pi u_b), sin(2 pi u_b)); element e takes
+ *   output e % 4 of its block.
+ * ------------------------------------------------------------------------- */
+static void philox_round(unsigned int c[4], const unsigned int k[2])
+{
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c[0];
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c[2];
+    const unsigned int hi0 = (unsigned int)(p0 >> 32), lo0 = (unsigned int)p0;
+    const unsigned int hi1 = (unsigned int)(p1 >> 32), lo1 = (unsigned int)p1;
+    const unsigned int n0 = hi1 ^ c[1] ^ k[0];
+    const unsigned int n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+void oracle_philox4x32_10(const unsigned int ctr_in[4], const unsigned int key_in[2], unsigned int out[4])
+{
+    unsigned int c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    unsigned int k[2] = {key_in[0], key_in[1]};
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k[0] += 0x9E3779B9u;
+            k[1] += 0xBB67AE85u;
+        }
+        philox_round(c, k);
+    }
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+int oracle_sample_batch(int N, int H, int J, const double *mean, const double *stdv,
+                        unsigned long long seed, unsigned long long stream, double *xi)
+{
+    if (N < 0 || H < 1 || J < 1) return -1;
+    const long long total = (long long)N * H * J;
+    const unsigned int key[2] = {(unsigned int)seed, (unsigned int)(seed >> 32)};
+    const double two_pi = 6.283185307179586476925286766559;
+    for (long long q = 0; q * 4 < total; ++q) {
+        const unsigned int ctr[4] = {(unsigned int)q, (unsigned int)((unsigned long long)q >> 32),
+                                     (unsigned int)stream, (unsigned int)(stream >> 32)};
+        unsigned int w[4];
+        oracle_philox4x32_10(ctr, key, w);
+        double u[4], z[4];
+        for (int i = 0; i < 4; ++i) u[i] = ((double)w[i] + 0.5) * (1.0 / 4294967296.0);
+        for (int p = 0; p < 2; ++p) {
+            const double r = sqrt(-2.0 * log(u[2 * p]));
+            z[2 * p] = r * cos(two_pi * u[2 * p + 1]);
+            z[2 * p + 1] = r * sin(two_pi * u[2 * p + 1]);
+        }
+        for (int i = 0; i < 4; ++i) {
+            const long long e = q * 4 + i;
+            if (e >= total) break;
+            const long long kj = e % ((long long)H * J);
+            xi[e] = mean[kj] + stdv[kj] * z[i];
+        }
+    }
+    return 0;
+}

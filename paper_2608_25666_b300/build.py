@@ -15,6 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 SRC = os.path.join(_HERE, "csrc", "prism_proj.cu")
 SRC_SERVER = os.path.join(_HERE, "csrc", "prism_server.cpp")
+SRC_MPPI = os.path.join(_HERE, "csrc", "prism_mppi.cu")
+SOURCES = [SRC, SRC_MPPI, SRC_SERVER]
 HDR = os.path.join(ROOT, "include", "prism_proj.h")
 OUT = os.path.join(_HERE, "_build", "libprism_proj.so")
 
@@ -31,12 +33,11 @@ def nvcc() -> str:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    newest = max(os.path.getmtime(SRC), os.path.getmtime(SRC_SERVER), os.path.getmtime(HDR))
+    newest = max([os.path.getmtime(f) for f in SOURCES] + [os.path.getmtime(HDR)])
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= newest:
         return OUT
     tmp = OUT + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp, SRC, SRC_SERVER,
-           "-lpthread"]
+    cmd = [nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES, "-lpthread"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)

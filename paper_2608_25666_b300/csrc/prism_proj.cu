@@ -246,6 +246,9 @@ struct SolveParams {
     int polish;                          // tensor cores: last iterations with the split K-apply
     int D;                               // multiplier rows per column: 4H-1 (ADMM) or H (PAPER)
     int tile0;                           // first tile of this problem in a batched launch
+    const float *s_mean, *s_std;         // [H][J]: draw xi = mean + std * z on the device (or NULL)
+    unsigned long long seed, sstream;    // Philox4x32-10 key and counter words 2-3
+    float *xi_out;                       // [N][H][J] drawn samples, or NULL
     float *out;
     float *primal;
     float *dual;
@@ -521,6 +524,48 @@ __host__ __device__ inline int tc_tmem_cols(int n)
 }
 
 // ===========================================================================
+// On-device sampling (Alg. 1, "draw n samples from N(nu, Sigma)"): Philox4x32-10
+// (Salmon et al., SC 2011) keyed by the seed, counter (block, stream), and the
+// Box-Muller transform; element e of the [N][H][J] batch is output e % 4 of
+// counter block e / 4, so any tile draws its own elements independently.
+// ===========================================================================
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// Four standard normals of counter block q.
+__device__ __forceinline__ void normals4(unsigned long long q, unsigned long long seed, unsigned long long stream,
+                                         float z[4])
+{
+    uint32_t c[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)stream, (uint32_t)(stream >> 32)};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const float u1 = fmaf((float)c[2 * p], 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+        const float u2 = fmaf((float)c[2 * p + 1], 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+        const float r = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        z[2 * p] = r * cs;
+        z[2 * p + 1] = r * sn;
+    }
+}
+
+// ===========================================================================
 // K3: persistent solve.  HQ = horizon steps per thread (H <= 4*HQ), MODE =
 // PRISM_MODE_ADMM / PRISM_MODE_PAPER, TC = K-apply on the tensor cores.
 // Shared memory: xs[(4HQ+2) x CP] floats (rows x_{-2}, x_{-1}, x_0 ..), rhs
@@ -667,7 +712,27 @@ solve_kernel(const __grid_constant__ LaunchParams P)
             dres[tid] = 0u;
         }
         __syncthreads();
-        {
+        if (p.s_mean) {
+            // draw the slab: elements [e0, e0 + Tt*HJ) of the batch, by counter blocks of 4
+            const unsigned long long e0 = (unsigned long long)n0 * HJ;
+            const unsigned long long e1 = e0 + (unsigned long long)Tt * HJ;
+            const unsigned long long q0b = e0 >> 2, q1b = (e1 + 3) >> 2;
+            for (unsigned long long q = q0b + tid; q < q1b; q += NTHREADS) {
+                float z[4];
+                normals4(q, p.seed, p.sstream, z);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned long long e = 4 * q + u;
+                    if (e < e0 || e >= e1) continue;
+                    const int el = (int)(e - e0);
+                    const int nl = el / HJ, rem = el - nl * HJ;
+                    const int k = rem / J, j = rem - k * J;
+                    const float v = fmaf(p.s_std[rem], z[u], p.s_mean[rem]);
+                    xs[(k + 2) * CP + nl * J + j] = v;
+                    if (p.xi_out) p.xi_out[e] = v;
+                }
+            }
+        } else {
             const float *src = (p.x_init ? p.x_init : p.xi) + (size_t)n0 * HJ;
             const int total = Tt * HJ;
             for (int e = tid; e < total; e += NTHREADS) {
@@ -865,6 +930,8 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     }
                     umma_commit(smem_addr(&mma_bar));
                 }
+                // every warp polls the mbarrier (measured: letting one warp poll and the
+                // others sleep in the block barrier made the iteration 1.6x slower)
                 const bool ok = mbar_wait(smem_addr(&mma_bar), mma_phase);
                 mma_phase ^= 1u;
                 if (__syncthreads_or(!ok)) {
@@ -1291,6 +1358,7 @@ prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const flo
     p.x_init = nullptr; p.dual_init = nullptr; p.dual_out = nullptr;
     p.D = (h->mode == PRISM_MODE_ADMM) ? 4 * h->H - 1 : h->H;
     p.tile0 = 0;
+    p.s_mean = nullptr; p.s_std = nullptr; p.seed = 0; p.sstream = 0; p.xi_out = nullptr;
     p.polish = (h->prec == PRISM_PREC_TF32) ? 0 : iters;
     p.out = out; p.primal = nullptr; p.dual = nullptr;
     return PRISM_OK;
@@ -1320,12 +1388,15 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
     if (!batched) fn = (mode == PRISM_MODE_ADMM) ? (tc ? v->admm_tc : v->admm) : (tc ? v->paper_tc : v->paper);
     else fn = (mode == PRISM_MODE_ADMM) ? (tc ? v->b_admm_tc : v->b_admm) : (tc ? v->b_paper_tc : v->b_paper);
     smem = (size_t)solve_smem(v->hq, n_max, MP_max, tc).total;
-    CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // The dynamic shared-memory limit is a property of the kernel function, shared
+    // by every handle and plan that launches it: only ever raise it.
+    cudaFuncAttributes fa;
+    CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)fn));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem)
+        CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   (int)cudaSharedmemCarveoutMaxShared));
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, (const void *)fn, NTHREADS, smem));
-    cudaFuncAttributes fa;
-    CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)fn));
     int smem_sm = 0, reserved = 0, regs_sm = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
     CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
@@ -1344,31 +1415,12 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
     v = pick_variant(h->H);
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", h->H);
     const bool tc = h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32;
-    fn = (h->mode == PRISM_MODE_ADMM) ? (tc ? v->admm_tc : v->admm) : (tc ? v->paper_tc : v->paper);
-    smem = (size_t)solve_smem(v->hq, h->n, h->MP, tc).total;
-    CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  (int)cudaSharedmemCarveoutMaxShared));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, (const void *)fn, NTHREADS, smem));
-    // The occupancy query under-reports for the tensor-core variant (it allows one
-    // block where the launch holds two); count registers and shared memory directly.
-    {
-        cudaFuncAttributes fa;
-        CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)fn));
-        int smem_sm = 0, reserved = 0, regs_sm = 0;
-        CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
-        CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, h->device));
-        CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, h->device));
-        const size_t per_block = smem + fa.sharedSizeBytes + (size_t)reserved;
-        const int by_smem = (int)(smem_sm / per_block);
-        const int by_regs = regs_sm / std::max(1, fa.numRegs * NTHREADS);
-        const int own = std::min(std::min(by_smem, by_regs), 2048 / NTHREADS);
-        blocks_per_sm = std::max(blocks_per_sm, own);
-    }
-    if (blocks_per_sm < 1) return fail(PRISM_ERR_UNSUPPORTED, "solve kernel does not fit on an SM (smem %zu)", smem);
+    int hq;
+    prism_status st = variant_config(h->H, h->mode, tc, false, h->n, h->MP, h->device, fn, smem, blocks_per_sm, hq);
+    if (st) return st;
     const int T = std::max(1, CMAX / h->J);
     const int ntiles = (batch + T - 1) / T;
-    grid = std::min(ntiles, blocks_per_sm * h->num_sms);
+    grid = std::max(1, std::min(ntiles, blocks_per_sm * h->num_sms));
     return PRISM_OK;
 }
 
@@ -1673,6 +1725,36 @@ prism_status prism_proj_solve_ex(prism_proj_t h, int batch, const float *q0, con
             return fail(PRISM_ERR_INVALID_ARG, "x_init must not alias out");
     }
     if (batch == 0) return PRISM_OK;
+    p.primal = primal_res;
+    p.dual = dual_res;
+    const Variant *v;
+    size_t smem;
+    int bps, grid;
+    solve_fn fn;
+    st = launch_config(h, batch, v, smem, bps, grid, fn);
+    if (st) return st;
+    fn<<<grid, NTHREADS, smem, (cudaStream_t)cuda_stream>>>(single_launch(p));
+    CUDA_TRY(cudaGetLastError());
+    return PRISM_OK;
+}
+
+prism_status prism_proj_sample_solve(prism_proj_t h, int batch, const float *q0, const float *v0, const float *mean,
+                                     const float *stdv, unsigned long long seed, unsigned long long stream_id,
+                                     int iters, double rho, float *out, float *samples_out, float *primal_res,
+                                     float *dual_res, void *cuda_stream)
+{
+    SolveParams p;
+    if (batch > 0 && (!mean || !stdv)) return fail(PRISM_ERR_INVALID_ARG, "null mean or std");
+    // the slab is drawn, so the samples pointer of the plain solve is not used
+    prism_status st = prepare_solve(h, batch, q0, v0, mean, iters, rho, out, p);
+    if (st) return st;
+    if (batch == 0) return PRISM_OK;
+    p.xi = nullptr;
+    p.s_mean = mean;
+    p.s_std = stdv;
+    p.seed = seed;
+    p.sstream = stream_id;
+    p.xi_out = samples_out;
     p.primal = primal_res;
     p.dual = dual_res;
     const Variant *v;

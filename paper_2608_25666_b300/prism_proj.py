@@ -73,6 +73,9 @@ def lib() -> ctypes.CDLL:
             L.prism_proj_solve_plain.argtypes = sig
             L.prism_proj_solve_host.argtypes = sig
             L.prism_proj_solve_ex.argtypes = [P, i, P, P, P, i, d, P, P, P, P, P]
+            L.prism_proj_sample_solve.argtypes = [P, i, P, P, P, P, ctypes.c_ulonglong, ctypes.c_ulonglong,
+                                                  i, d, P, P, P, P, P]
+            L.prism_proj_sample_solve.restype = i
             L.prism_proj_check_fp64.argtypes = [P, i, P, P, P, P, P]
             L.prism_proj_shift_state.argtypes = [P, i, i, P, P, P]
             L.prism_proj_get_factor.argtypes = [P, P, P]
@@ -100,6 +103,10 @@ def lib() -> ctypes.CDLL:
             L.prism_server_destroy.argtypes = [P]
             for name in ("create", "add_controller", "submit", "wait", "stats", "reset_stats", "destroy"):
                 getattr(L, "prism_server_" + name).restype = i
+            L.prism_mppi_workspace_bytes.argtypes = [i, i, i]
+            L.prism_mppi_workspace_bytes.restype = ctypes.c_size_t
+            L.prism_mppi_update.argtypes = [i, i, i, P, d, d, P, P, P, P, P, ctypes.c_size_t, P]
+            L.prism_mppi_update.restype = i
             L.prism_status_string.argtypes = [i]
             L.prism_status_string.restype = ctypes.c_char_p
             L.prism_last_error.argtypes = []
@@ -224,6 +231,23 @@ class Projector:
 
         x, pr, du = self._solve(fn, q0, v0, samples, iters, rho, out, primal, dual, stream, want_res)
         return x, pr, du, dual_out
+
+    def sample_solve(self, q0, v0, mean, std, N: int, iters: int, seed: int, stream_id: int,
+                     rho: float | None = None, want_samples: bool = False, stream=None):
+        """prism_proj_sample_solve: draw N samples of N(mean, std^2) on the device and project
+        them; returns (x, primal, dual, samples or None)."""
+        import torch
+        _need_cuda_f32("q0", q0, (self.J,))
+        _need_cuda_f32("v0", v0, (self.J,))
+        _need_cuda_f32("mean", mean, (self.H, self.J))
+        _need_cuda_f32("std", std, (self.H, self.J))
+        out, primal, dual = self._outputs(N, None, None, None, True)
+        xs = torch.empty((N, self.H, self.J), dtype=torch.float32, device=mean.device) if want_samples else None
+        rho = self.rho if rho is None else rho
+        _check(lib().prism_proj_sample_solve(self._h, int(N), _ptr(q0), _ptr(v0), _ptr(mean), _ptr(std),
+                                             int(seed), int(stream_id), int(iters), float(rho), _ptr(out),
+                                             _ptr(xs), _ptr(primal), _ptr(dual), _stream_ptr(stream)))
+        return out, primal, dual, xs
 
     def solve_plain(self, q0, v0, samples, iters: int, rho: float | None = None, out=None,
                     primal=None, dual=None, stream=None, want_res: bool = True):
@@ -433,3 +457,21 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def mppi_update(cost, x, temperature: float, eps: float = 0.0, workspace=None, stream=None):
+    """prism_mppi_update: (mean [H,J], var [H,J], weights [N]) from costs [N] and x [N,H,J]."""
+    import torch
+    N, H, J = (int(v) for v in x.shape)
+    _need_cuda_f32("x", x, (N, H, J))
+    _need_cuda_f32("cost", cost, (N,))
+    nbytes = int(lib().prism_mppi_workspace_bytes(N, H, J))
+    if workspace is None:
+        workspace = torch.empty(max(1, nbytes // 4 + 1), dtype=torch.float32, device=x.device)
+    mean = torch.empty((H, J), dtype=torch.float32, device=x.device)
+    var = torch.empty((H, J), dtype=torch.float32, device=x.device)
+    w = torch.empty((N,), dtype=torch.float32, device=x.device)
+    _check(lib().prism_mppi_update(N, H, J, _ptr(cost), float(temperature), float(eps), _ptr(x), _ptr(mean),
+                                   _ptr(var), _ptr(w), _ptr(workspace), workspace.numel() * 4,
+                                   _stream_ptr(stream)))
+    return mean, var, w
