@@ -34,6 +34,28 @@ UNIT = "trajectories/s"
 N_INPUTS = 64
 PRECS = {"fp32": 0, "tf32x3": 3}
 
+# DRAM bytes (read + write) of one launch of the solve kernel on this workload,
+# from one ncu capture (profiles/solve_kernel_realistic_N4096_J12_H50.md), keyed
+# by the SHA-256 prefix of the kernel source it was taken on: a changed kernel
+# reports null until it is captured again.
+MEASURED_TRAFFIC = {
+    "fp32": {"kernel_source_sha256_16": "64192e7a23c8e870", "bytes": 9912576},
+}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_2608_25666_b300", "csrc", "prism_proj.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic(prec: str):
+    rec = MEASURED_TRAFFIC.get(prec)
+    if not rec or rec["kernel_source_sha256_16"] != kernel_source_hash():
+        return None
+    return rec["bytes"]
+
 
 def flops_per_column_iteration(H: int) -> int:
     """Algorithmic FP32 flops of one iteration of one column (ADMM mode).
@@ -173,27 +195,46 @@ def cpu_oracle_sample(seconds_target: float = 15.0, rank_step: int = 0):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores, on the same
+    workload (realistic MPC step); each step projects a bounded random column sample of
+    that step's batch, sized so that the whole --steps/--warmup run takes ~2-3 minutes."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    per_step = []
+    import oracle
+    w = WORKLOAD
     cores = os.cpu_count() or 1
-    desc = ""
-    budget = max(5.0, 120.0 / max(1, args.steps + args.warmup))
+    total_budget_s = 150.0
+    per_step_s = max(0.05, min(20.0, total_budget_s / max(1, args.steps + args.warmup)))
+    # calibrate the oracle's speed once
+    b = workloads.make_batch(w, step=0)
+    rng = np.random.default_rng(0)
+    ncal = max(cores * 4, 32)
+    t0 = time.perf_counter()
+    oracle.solve_batch(b["xi"], b["q0"], b["v0"], b["bounds"], w.dt, w.iters, w.rho,
+                       cols=rng.choice(w.N * w.J, ncal, replace=False), nthreads=cores)
+    per_col = (time.perf_counter() - t0) / ncal
+    ncols = int(max(w.J, min(w.N * w.J, per_step_s / max(per_col, 1e-9))))
+    batches = [workloads.make_batch(w, step=s) for s in range(min(4, args.steps + args.warmup))]
+    per_step = []
     for s in range(args.warmup + args.steps):
-        v, cores, desc = cpu_oracle_sample(seconds_target=min(20.0, budget), rank_step=s % N_INPUTS)
+        bb = batches[s % len(batches)]
+        cols = rng.choice(w.N * w.J, ncols, replace=False)
+        t0 = time.perf_counter()
+        oracle.solve_batch(bb["xi"], bb["q0"], bb["v0"], bb["bounds"], w.dt, w.iters, w.rho, cols=cols,
+                           nthreads=cores)
+        dt = time.perf_counter() - t0
         if s >= args.warmup:
-            per_step.append(v)
+            per_step.append((ncols / w.J) / dt)
     value = statistics.mean(per_step)
+    desc = (f"{ncols} random columns (= {ncols / w.J:.1f} trajectories) of each {w.N}x{w.J}x{w.H} step, "
+            f"{w.iters} iterations, ~{per_step_s:.2f} s per step, OpenMP over columns")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": WORKLOAD.N / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": w.N / value * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; no dataset)",
             "config": config_dict(),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -278,7 +319,7 @@ def run_serving(args):
     from paper_2608_25666_b300 import serving
     ws, rank, local = dist_setup()
     prec = PRECS[args.prec]
-    ctrls = serving.make_controllers(args.controllers, seed=1004 + 1000 * rank, prec=prec)
+    ctrls = serving.make_controllers(args.controllers, seed=1004 + 1000 * rank, prec=prec, n_hi=args.n_hi)
     S = pp.Server(mem_budget_bytes=8 << 30, max_inflight=16, deadline_ms=20.0)
     # warm-up: one request per controller
     serving.run(S, ctrls, 2)
@@ -295,7 +336,8 @@ def run_serving(args):
                 "warmup": 2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.prec == "fp32" else "f32 (K-apply: tf32 split on tensor cores)",
                 "data": "synthetic (seeded; no dataset)",
-                "config": {"workload": f"serving: {len(ctrls)} controllers, one request per 20 ms step each, "
+                "config": {"workload": f"serving: {len(ctrls)} controllers (N log-uniform 128..{args.n_hi}), "
+                                       "one request per 20 ms step each, "
                                        "exponential jitter (mean 2 ms), all controllers within 6.4 ms once per "
                                        "second, 150 iterations, warm-started multipliers, 8 GB budget",
                            "controllers": [(c["J"], c["H"], c["N"]) for c in ctrls]},
@@ -381,7 +423,7 @@ def run_sigma_eff(args):
     import oracle
     from paper_2608_25666_b300 import prism_proj as pp
     ws, rank, local = dist_setup()
-    N, sigma, iters = 200_000, 10.0, 500
+    N, sigma, iters = 200_000, 10.0, 5000
     bounds = np.array([-1e6, 1e6, -1.0, 1.0, -2.0, 2.0, -4.0, 4.0]).reshape(8, 1)
     q0 = torch.zeros(1, device="cuda")
     v0 = torch.zeros(1, device="cuda")
@@ -397,13 +439,14 @@ def run_sigma_eff(args):
         e1.record()
         torch.cuda.synchronize()
         xn = x[:, 1:, 0].double()
-        cols = np.arange(0, N, N // 50)
-        o = oracle.solve_batch(xs.cpu().numpy()[cols], np.zeros(1), np.zeros(1), bounds, dt, iters, 1.0)
+        cols = np.arange(0, N, N // 20)
+        o = oracle.solve_batch(xs.cpu().numpy()[cols], np.zeros(1), np.zeros(1), bounds, dt, iters, 1.0,
+                               nthreads=os.cpu_count() or 1)
         dx = float(np.max(np.abs(x.cpu().numpy()[cols] - o["x"])))
         res.append({"H": H, "dt": dt, "sigma_eff_pooled": float(xn.std()),
                     "sigma_eff_mean_per_step": float(xn.std(dim=0).mean()),
                     "max_violation": float(pr.max()), "ms": e0.elapsed_time(e1),
-                    "parity_max_abs_dx_50_columns": dx})
+                    "parity_max_abs_dx_20_columns": dx})
         P.close()
     if rank == 0:
         print(json.dumps({"metric": "sigma_eff of QP-projected samples", "value": None, "unit": "rad/s",
@@ -434,6 +477,7 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=list(PRECS))
     ap.add_argument("--workload", default="realistic", choices=["realistic", "batched", "serving", "precision", "sigma_eff"])
     ap.add_argument("--controllers", type=int, default=32)
+    ap.add_argument("--n-hi", type=int, default=8192, help="serving: largest controller batch N")
     ap.add_argument("--nprob", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -543,7 +587,7 @@ def main():
     achieved = flops / avg_launch_s / 1e12
     peak = peak_fp32_tflops(q["num_sms"], 2032.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": measured_traffic(args.prec),
                 "kernel": f"solve_kernel (persistent ADMM, K-apply {args.prec})",
                 "peak_basis": f"FP32 FMA issue rate {q['num_sms']} SMs x 128 lanes x 2 flop x 2032 MHz"
                               " (max SM clock; derived, no measured FP32 peak)",
