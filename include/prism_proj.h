@@ -112,7 +112,7 @@ prism_status prism_proj_create(int J, int H, double dt,
  *   and kb = [M^-1]_{1:H,H+1} on the device (FP64, plus an FP32 copy used by
  *   the solve).  rho > 0 is the paper's penalty delta.  prec selects the
  *   K-apply of prism_proj_solve: PRISM_PREC_FP32 (FP32 pipe, any H) or
- *   PRISM_PREC_TF32X3 / PRISM_PREC_TF32 (tensor cores, H <= 105; larger H
+ *   PRISM_PREC_TF32X3 / PRISM_PREC_TF32 (tensor cores, H <= 116; larger H
  *   returns PRISM_ERR_UNSUPPORTED).  Enqueued on
  *   cuda_stream; re-factoring a handle replaces its factor (the caller orders
  *   it after solves that still use the old one).

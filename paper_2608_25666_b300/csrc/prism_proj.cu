@@ -121,7 +121,7 @@ struct prism_proj_s {
     float *d_Kt32 = nullptr;             // [n][MP] transposed K, FP32, zero padded
     float *d_kb32 = nullptr;             // [MP]
     float *d_wp = nullptr;               // [PRISM_MAX_H] position-row weights
-    float *d_Khi = nullptr, *d_Klo = nullptr;   // [n][n] tf32 split of K'
+    float *d_Khi = nullptr, *d_Klo = nullptr;   // [n][n+1] tf32 split of [K' | kb']
     int *d_err = nullptr;                // tensor-core wait timeout flag
     double *d_wfull = nullptr;           // factor input: per-row weights (4 blocks x H)
     // plain comparator workspace
@@ -210,15 +210,19 @@ __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wr
         const int j = e / MP, i = e % MP;
         Kt32[e] = (i < n) ? (float)K64[i * n + j] : 0.0f;
     }
-    // tf32 split of K' for the tensor-core K-apply: hi = K' rounded to tf32,
-    // lo = the remainder in FP32 (the tensor core keeps its leading tf32 bits).
-    for (int e = tid; e < n * n; e += nth) {
+    // tf32 split of [K' | kb'] (n x (n+1)) for the tensor-core K-apply: hi = the
+    // entry rounded to tf32, lo = the remainder in FP32 (the tensor core keeps its
+    // leading tf32 bits).
+    __syncthreads();
+    for (int e = tid; e < n * (n + 1); e += nth) {
         uint32_t r;
-        const float kf = (float)K64[e];
+        const int i = e / (n + 1), j = e - i * (n + 1);
+        const double kv = (j < n) ? K64[i * n + j] : kb64[i];
+        const float kf = (float)kv;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(kf));
         const float hi = __uint_as_float(r);
         Khi32[e] = hi;
-        Klo32[e] = (float)(K64[e] - (double)hi);
+        Klo32[e] = (float)(kv - (double)hi);
     }
 }
 
@@ -237,8 +241,8 @@ struct SolveParams {
     const float *__restrict__ Kt;        // [n][MP]
     const float *__restrict__ kb;        // [MP]
     const float *__restrict__ wp;        // [>= H]
-    const float *__restrict__ Khi;       // [n][n] tf32 high part of K' (tensor-core path)
-    const float *__restrict__ Klo;       // [n][n] remainder K' - Khi
+    const float *__restrict__ Khi;       // [n][n+1] tf32 high part of [K' | kb'] (tensor-core path)
+    const float *__restrict__ Klo;       // [n][n+1] remainder [K' | kb'] - Khi
     int *err;                            // set to 1 if a tensor-core wait ran out
     const float *x_init;                 // [N][H][J] warm-start iterate or NULL (x^0 = xi)
     const float *dual_init;              // [N][D][J] warm-start multiplier or NULL (0)
@@ -261,7 +265,6 @@ struct LaunchParams {
     const SolveParams *many;   // nullptr: the launch solves `one`
     int nprob, ntiles;
     int n_max, MP_max;         // shared-memory layout bounds over the launch's problems
-    int tmem_cols;             // tensor memory columns allocated per block
 };
 
 // Two-sided bounds of one column in the device units (computed in double,
@@ -345,6 +348,24 @@ __device__ __forceinline__ void load_xwin(const float *__restrict__ xs, int CP, 
     float run = 0.0f;
 #pragma unroll
     for (int r = 0; r < HQ; ++r) run += X.w[r + 2];
+    X.pre = excl_prefix4(run, b);
+}
+
+// The x window from this quarter's time steps held in registers: the two halo
+// steps come from the previous quarter's thread (zero for quarter 0).
+template <int HQ>
+__device__ __forceinline__ void xwin_from_regs(const float xq[HQ], int b, XWin<HQ> &X)
+{
+    const float h0 = __shfl_up_sync(0xffffffffu, xq[HQ - 2 >= 0 ? HQ - 2 : 0], 1, 4);
+    const float h1 = __shfl_up_sync(0xffffffffu, xq[HQ - 1], 1, 4);
+    X.w[0] = b > 0 ? h0 : 0.0f;
+    X.w[1] = b > 0 ? h1 : 0.0f;
+    float run = 0.0f;
+#pragma unroll
+    for (int r = 0; r < HQ; ++r) {
+        X.w[r + 2] = xq[r];
+        run += xq[r];
+    }
     X.pre = excl_prefix4(run, b);
 }
 
@@ -512,15 +533,47 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
     for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
 
+// This quarter-thread's HQ time steps from tensor memory: 16x128b loads at
+// columns 4k (k < HQ) give thread t lane t/4 and lane t/4 + 8 of column
+// 4k + t%4; `upper` picks the second.  All loads are issued before one wait,
+// and the registers pass through the wait so no use is scheduled before it.
+template <int HQ>
+__device__ __forceinline__ void tmem_ld_quarter(uint32_t taddr, bool upper, float out[HQ])
+{
+    constexpr int G = 4;   // loads per wait
+#pragma unroll
+    for (int k0 = 0; k0 < HQ; k0 += G) {
+        uint32_t lo[G], hi[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (k0 + g < HQ)
+                asm volatile("tcgen05.ld.sync.aligned.16x128b.x1.b32 {%0, %1}, [%2];"
+                             : "=r"(lo[g]), "=r"(hi[g]) : "r"(taddr + (uint32_t)(4 * (k0 + g))));
+            else
+                lo[g] = hi[g] = 0u;
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(lo[0]), "+r"(hi[0]), "+r"(lo[1]), "+r"(hi[1]), "+r"(lo[2]), "+r"(hi[2]),
+                       "+r"(lo[3]), "+r"(hi[3]) :: "memory");
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (k0 + g < HQ) out[k0 + g] = __uint_as_float(upper ? hi[g] : lo[g]);
+    }
+}
+
 __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// TC operand sizes for reduced size n = H - 1.
-__host__ __device__ inline int tc_kd(int n) { return round_up(n, 8); }
-__host__ __device__ inline int tc_ndim(int n) { return round_up(n, 16); }
-__host__ __device__ inline int tc_tmem_cols(int n)
+// TC operand sizes.  The reduction (K) runs over the n = H - 1 right-hand-side
+// rows plus one column carrying v0 (so D = K' rhs + kb' v0), padded to the
+// 8-wide MMA granule.  The outputs (N) are the 4*HQ time steps of the four
+// quarters, interleaved (D column 4k + b holds x_{b*HQ + k}) so that one
+// 16x128b tensor-memory load hands each quarter-thread its own time steps.
+__host__ __device__ inline int tc_kd(int n) { return round_up(n + 1, 8); }
+__host__ __device__ constexpr int tc_nrows(int hq) { return round_up(4 * hq, 8); }
+// Tensor-memory columns per block: the readback touches columns < 16*ceil(HQ/4).
+__host__ __device__ constexpr int tc_tmem_cols(int hq)
 {
-    const int nd = tc_ndim(n);
-    return nd <= 32 ? 32 : nd <= 64 ? 64 : nd <= 128 ? 128 : 256;
+    return round_up(4 * hq, 16) <= 32 ? 32 : round_up(4 * hq, 16) <= 64 ? 64 : round_up(4 * hq, 16) <= 128 ? 128 : 256;
 }
 
 // ===========================================================================
@@ -571,10 +624,11 @@ __device__ __forceinline__ void normals4(unsigned long long q, unsigned long lon
 // Shared memory: xs[(4HQ+2) x CP] floats (rows x_{-2}, x_{-1}, x_0 ..), rhs
 // [4HQ x CP], kb, wp, v0c, dres; the FP32-pipe variant adds Kt[n x MP]; the
 // tensor-core variant adds the operands A (128 x KD: the tile's right-hand
-// sides, tf32 high parts in rows 0..63, remainders in rows 64..127) and B
-// (K' high and low parts, ND x KD each) and keeps D (128 x ND fp32) in tensor
-// memory.  Summing both halves of D gives K'(rhs_hi + rhs_lo) with the
-// products of the two tf32 parts of both operands, i.e. FP32-level accuracy.
+// sides and, in column n, v0; tf32 high parts in rows 0..63, remainders in rows
+// 64..127) and B ([K' | kb'] high and low parts, ND x KD each) and keeps D
+// (64 x ND fp32) in tensor memory.  Three MMAs per K-step (A_hi B_hi, A_hi B_lo,
+// A_lo B_hi) accumulate K' rhs + kb' v0 with the products of the two tf32 parts
+// of both operands, i.e. FP32-level accuracy.
 // ===========================================================================
 template <int HQ>
 __host__ __device__ constexpr int solve_min_blocks() { return HQ <= 17 ? 2 : 1; }
@@ -590,15 +644,15 @@ __host__ __device__ inline SolveSmem solve_smem(int hq, int n, int MP, bool tc)
     SolveSmem L;
     int off = 0;
     if (tc) {
-        const int KD = tc_kd(n), ND = tc_ndim(n);
+        const int KD = tc_kd(n), ND = tc_nrows(hq);
         L.a = off;   off += 128 * KD * 4;
         L.bhi = off; off += ND * KD * 4;
         L.blo = off; off += ND * KD * 4;
     } else {
         L.a = L.bhi = L.blo = 0;
     }
-    L.xs = off;  off += (HP + 2) * CP * 4;
-    L.rhs = off; off += HP * CP * 4;          // SIMT: rhs; tensor cores: lower-half partial sums
+    L.xs = off;  off += (HP + 2) * CP * 4;   // rows x_{-2} .. x_{HP-1}
+    L.rhs = off; off += tc ? 0 : HP * CP * 4;   // SIMT only
     L.kt = off;  off += tc ? 0 : n * MP * 4;
     L.kb = off;  off += MP * 4;
     L.wp = off;  off += 4 * HP * 4;        // per-row weights: position, velocity, acceleration, jerk
@@ -614,6 +668,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
 {
     constexpr int HP = 4 * HQ;
     constexpr int CP = col_stride(HQ);
+    constexpr int TMEM_COLS = tc_tmem_cols(HQ);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mma_bar;
@@ -637,12 +692,17 @@ solve_kernel(const __grid_constant__ LaunchParams P)
     const int c = tid >> 2;       // column in tile
     const int b = tid & 3;        // time quarter
     const int i0 = b * HQ;
+    // Tensor cores: MMA row (A row, D row) of this column, chosen so that the
+    // column's D row sits in a tensor-memory lane this warp can read: the M = 64
+    // accumulator keeps row r in lane 32 (r / 16) + r % 16, warp w reads lanes
+    // 32 (w % 4) .. + 31, and a 16x128b load gives thread t lanes t/4 and t/4 + 8.
+    const int arow = 16 * (warp & 3) + 8 * (warp >> 2) + (lane >> 2);
 
     uint32_t tbase = 0, mma_phase = 0;
     if (TC) {
         if (warp == 0) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                         :: "r"(smem_addr(&tmem_slot)), "r"(P.tmem_cols));
+                         :: "r"(smem_addr(&tmem_slot)), "r"(TMEM_COLS));
             asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         }
         if (tid == 0) {
@@ -654,7 +714,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         tbase = tmem_slot;
     }
-    bool aborted = false;
+    bool aborted = false, timed_out = false;
     int cur = -1;
 
     for (int tile = blockIdx.x; tile < P.ntiles && !aborted; tile += gridDim.x) {
@@ -674,7 +734,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
         const float rho = p.rho;
         const float wv = p.wv, wa0 = p.wa0, wa = p.wa, wj0 = p.wj0, wj = p.wj;
         const int iters = p.iters, polish = p.polish;
-        const int KD = tc_kd(n), ND = tc_ndim(n);
+        const int KD = tc_kd(n), ND = tc_nrows(HQ);
         const int n0 = (tile - p.tile0) * p.T;
         const int Tt = min(p.T, p.N - n0);
         const int Ct = Tt * J;
@@ -692,13 +752,17 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 wjs[e] = (e >= 1 && e < H) ? (e == 1 ? p.wj0 : p.wj) : 0.0f;
             }
             if (TC) {
-                // B = K' (rows i, reduction j) split in tf32 high / low parts; A
-                // zeroed (its padding columns k >= n must stay zero).
+                // B = [K' | kb'] (rows = D columns in the interleaved output order,
+                // reduction j) split in tf32 high / low parts; A zeroed (its padding
+                // columns k > n must stay zero).
                 for (int e = tid; e < ND * KD; e += NTHREADS) {
-                    const int i = e / KD, j = e - i * KD;
-                    const bool in = i < n && j < n;
-                    *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(i, j, KD)) = in ? p.Khi[i * n + j] : 0.0f;
-                    *reinterpret_cast<float *>(smem_raw + L.blo + cm_off(i, j, KD)) = in ? p.Klo[i * n + j] : 0.0f;
+                    const int pr = e / KD, j = e - pr * KD;
+                    const int xt = (pr & 3) * HQ + (pr >> 2);   // time step of D column pr
+                    const int i = xt - 1;                       // its row of [K' | kb']
+                    const bool in = xt >= 1 && xt <= n && j <= n;   // column n: kb'
+                    const int src = i * (n + 1) + j;
+                    *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, j, KD)) = in ? p.Khi[src] : 0.0f;
+                    *reinterpret_cast<float *>(smem_raw + L.blo + cm_off(pr, j, KD)) = in ? p.Klo[src] : 0.0f;
                 }
                 for (int e = tid; e < 128 * KD; e += NTHREADS) reinterpret_cast<float *>(As)[e] = 0.0f;
             }
@@ -758,7 +822,16 @@ solve_kernel(const __grid_constant__ LaunchParams P)
             for (int r = 0; r < HQ; ++r) xi[r] = xs[(i0 + r + 2) * CP + c];
         }
         __syncthreads();
-        if (b == 0) xs[2 * CP + c] = colv ? v0j : 0.0f;
+        if (b == 0) {
+            xs[2 * CP + c] = colv ? v0j : 0.0f;
+            if (TC) {
+                // column n of A: v0 of this column, split like the right-hand sides
+                const float v = colv ? v0j : 0.0f;
+                const float hi = tf32_rna(v);
+                *reinterpret_cast<float *>(As + cm_off(arow, n, KD)) = hi;
+                *reinterpret_cast<float *>(As + 64 * KD * 4 + cm_off(arow, n, KD)) = v - hi;
+            }
+        }
         __syncthreads();
 
         // state
@@ -806,7 +879,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
 
         for (int l = 0; l < iters; ++l) {
             // ---- stencil phase: a3 slack / clip, a4 Fh^T, a6 multiplier -> rhs
-            if (l > 0) load_xwin<HQ>(xs, CP, c, b, X);
+            if (!TC && l > 0) load_xwin<HQ>(xs, CP, c, b, X);
             Rows<HQ> s;
             float g[HQ], rv[HQ];
             // Rows that do not exist carry zero weight, so their multiplier state may
@@ -895,8 +968,9 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 kapply(xs, rhs, Kts, kbs, v0c, dres, n, p.MP, CP, ncg, last);
                 __syncthreads();
             } else {
-                // rhs -> A_hi (tf32 high parts) and A_lo (remainders), rows = columns c,
-                // K = i - 1.  Iterations before the polish phase use the high parts only.
+                // rhs -> A_hi (tf32 high parts) and A_lo (remainders) in this column's
+                // MMA row, K = i - 1.  Iterations before the polish phase use the high
+                // parts only.
                 const bool split = l >= iters - polish;
                 const int a_lo = 64 * KD * 4;   // byte offset of A_lo after A_hi
 #pragma unroll
@@ -904,14 +978,23 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     const int i = i0 + r;
                     if (i >= 1 && i < H) {
                         const float hi = tf32_rna(rv[r]);
-                        *reinterpret_cast<float *>(As + cm_off(c, i - 1, KD)) = hi;
-                        if (split) *reinterpret_cast<float *>(As + a_lo + cm_off(c, i - 1, KD)) = rv[r] - hi;
+                        *reinterpret_cast<float *>(As + cm_off(arow, i - 1, KD)) = hi;
+                        if (split) *reinterpret_cast<float *>(As + a_lo + cm_off(arow, i - 1, KD)) = rv[r] - hi;
                     }
                 }
+                // A visible to the tensor core, the previous readback of D finished;
+                // a warp whose MMA wait ran out stops the whole block here
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                if (__syncthreads_or(timed_out)) {
+                    if (tid == 0 && p.err) atomicExch(p.err, 1);
+                    aborted = true;
+                    break;
+                }
                 // ---- a5: K-apply on the tensor cores, one M=64 accumulator:
-                // D[c][i] = sum_j (A_hi Khi + A_hi Klo + A_lo Khi)[c][j][i]
+                // D[row][col] = sum_j (A_hi Bhi + A_hi Blo + A_lo Bhi), j over the
+                // right-hand-side rows and the v0 column, B = [K' | kb'] in the
+                // interleaved output order
                 if (tid == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t idesc = umma_idesc_tf32(64, ND);
@@ -932,51 +1015,45 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 }
                 // every warp polls the mbarrier (measured: letting one warp poll and the
                 // others sleep in the block barrier made the iteration 1.6x slower)
-                const bool ok = mbar_wait(smem_addr(&mma_bar), mma_phase);
+                const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mma_bar), mma_phase));
                 mma_phase ^= 1u;
-                if (__syncthreads_or(!ok)) {
-                    if (tid == 0 && p.err) atomicExch(p.err, 1);
-                    aborted = true;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                // readback: with M = 64, row r of D sits in TMEM lane 32 (r / 16) + r % 16,
-                // so warp quarter q holds columns 16q .. 16q+15 in its first 16 lanes;
-                // the two warps of a quarter split the N = ND outputs in halves.
-                {
-                    const int q = warp & 3, half = warp >> 2;
-                    const int cc = 16 * q + (lane & 15);
-                    const int NH = ND >> 1;
-                    const uint32_t tl = tbase + ((uint32_t)(32 * q) << 16);
-                    const bool act = lane < 16;
-                    const float v0v = v0c[cc];
-                    float dm = 0.0f;
-                    for (int ch = 0; ch < NH; ch += 16) {
-                        float d[16];
-                        tmem_ld16(tl + (uint32_t)(half * NH + ch), d);
-                        if (act) {
+                if (!ok) {
+                    timed_out = true;   // X keeps the old iterate; the block stops at the next barrier
+                } else {
+                    // readback straight into the x window: D column 4k + b holds
+                    // x_{b*HQ + k}; lane t/4 (warps 0-3) or t/4 + 8 (warps 4-7) is
+                    // this thread's column
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t tl = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+                    const bool upper = warp >= 4;
+                    float xn[HQ];
+                    tmem_ld_quarter<HQ>(tl, upper, xn);
+                    if (b == 0) xn[0] = colv ? v0j : 0.0f;   // x_0 = v0 exactly
+                    if (last) {
+                        float dm = 0.0f;
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) {
-                                const int i = half * NH + ch + e;
-                                if (ch + e < NH && i < n) {
-                                    const float nv = fmaf(kbs[i], v0v, d[e]);
-                                    float *dst = xs + (i + 3) * CP + cc;
-                                    if (last) dm = fmaxf(dm, fabsf(nv - *dst));
-                                    *dst = nv;
-                                }
-                            }
+                        for (int r = 0; r < HQ; ++r) {
+                            const int i = i0 + r;
+                            if (i >= 1 && i < H) dm = fmaxf(dm, fabsf(xn[r] - X.w[r + 2]));
                         }
+                        dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, 1, 4));
+                        dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, 2, 4));
+                        if (b == 0) dres[c] = __float_as_uint(dm);
                     }
-                    if (last && act) atomicMax(&dres[cc], __float_as_uint(dm));
+                    xwin_from_regs<HQ>(xn, b, X);
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncthreads();
+            }
+        }
+        if (TC && !aborted) {
+            if (__syncthreads_or(timed_out)) {
+                if (tid == 0 && p.err) atomicExch(p.err, 1);
+                aborted = true;
             }
         }
         if (aborted) break;
 
         // ---- a7: residuals and store
-        load_xwin<HQ>(xs, CP, c, b, X);
+        if (!TC) load_xwin<HQ>(xs, CP, c, b, X);
         float viol = 0.0f;
         {
             float cs = X.pre;
@@ -1053,6 +1130,12 @@ solve_kernel(const __grid_constant__ LaunchParams P)
             if (p.primal) p.primal[col] = viol;
             if (p.dual) p.dual[col] = __uint_as_float(dres[c]);
         }
+        if (TC) {
+            // the final iterate is in registers: back to the tile for a coalesced store
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) xs[(i0 + r + 2) * CP + c] = X.w[r + 2];
+            __syncthreads();
+        }
         {
             float *dst = p.out + (size_t)n0 * HJ;
             const int total = Tt * HJ;
@@ -1067,7 +1150,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (warp == 0)
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(P.tmem_cols));
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(TMEM_COLS));
     }
 }
 
@@ -1315,7 +1398,7 @@ bool tc_fits(int H)
     const Variant *v = pick_variant(H);
     if (!v) return false;
     const int n = H - 1;
-    return solve_smem(v->hq, n, (n + 3) & ~3, true).total <= 220 * 1024 && tc_ndim(n) <= 256;
+    return solve_smem(v->hq, n, (n + 3) & ~3, true).total <= 220 * 1024 && tc_nrows(v->hq) <= 256;
 }
 
 bool is_finite(double v) { return std::isfinite(v); }
@@ -1373,7 +1456,6 @@ LaunchParams single_launch(const SolveParams &p)
     lp.ntiles = p.ntiles;
     lp.n_max = p.n;
     lp.MP_max = p.MP;
-    lp.tmem_cols = tc_tmem_cols(p.n);
     return lp;
 }
 
@@ -1653,8 +1735,8 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
         CUDA_TRY(cudaMalloc(&h->d_kb32, sizeof(float) * std::max(MP, 4)));
         CUDA_TRY(cudaMalloc(&h->d_wp, sizeof(float) * PRISM_MAX_H));
         CUDA_TRY(cudaMalloc(&h->d_wfull, sizeof(double) * 4 * H));
-        CUDA_TRY(cudaMalloc(&h->d_Khi, sizeof(float) * std::max(n * n, 4)));
-        CUDA_TRY(cudaMalloc(&h->d_Klo, sizeof(float) * std::max(n * n, 4)));
+        CUDA_TRY(cudaMalloc(&h->d_Khi, sizeof(float) * std::max(n * (n + 1), 4)));
+        CUDA_TRY(cudaMalloc(&h->d_Klo, sizeof(float) * std::max(n * (n + 1), 4)));
         CUDA_TRY(cudaMalloc(&h->d_err, sizeof(int)));
         CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
     }
@@ -2019,7 +2101,6 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             g.lp.ntiles = tiles;
             g.lp.n_max = n_max;
             g.lp.MP_max = MP_max;
-            g.lp.tmem_cols = tc_tmem_cols(n_max);
             int hq;
             st = variant_config(Hmax, g.mode, g.tc, true, n_max, MP_max, dev, g.fn, g.smem, g.bps, hq);
             if (st) break;
@@ -2067,7 +2148,6 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             if (can_switch) {
                 PlanGroup alt = g;
                 alt.tc = !g.tc;
-                if (alt.tc) alt.lp.tmem_cols = tc_tmem_cols(alt.lp.n_max);
                 int hq;
                 int Hmax = 2;
                 for (int k : g.members) Hmax = std::max(Hmax, probs[k].h->H);

@@ -20,7 +20,7 @@ import numpy as np
 MODE_ADMM, MODE_PAPER = 0, 1
 SCALE_ROWNORM, SCALE_NONE = 0, 1
 PREC_FP32, PREC_BF16X3, PREC_TF32, PREC_TF32X3 = 0, 1, 2, 3
-TC_MAX_H = 105
+TC_MAX_H = 116
 MAX_H, MAX_J = 132, 64
 
 STATUS = {0: "PRISM_OK", 1: "PRISM_ERR_INVALID_ARG", 2: "PRISM_ERR_NOT_FACTORED",

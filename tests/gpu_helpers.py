@@ -16,7 +16,7 @@ def to_dev(b):
             torch.from_numpy(b["v0"]).cuda())
 
 
-TC_MAX_H = 105       # largest horizon of the tensor-core K-apply
+TC_MAX_H = 116       # largest horizon of the tensor-core K-apply
 
 
 def gpu_solve(b, iters, rho=1.0, mode=pp.MODE_ADMM, scale=pp.SCALE_ROWNORM, kernel="persistent",
