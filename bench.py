@@ -40,6 +40,7 @@ PRECS = {"fp32": 0, "tf32x3": 3}
 # reports null until it is captured again.
 MEASURED_TRAFFIC = {
     "fp32": {"kernel_source_sha256_16": "64192e7a23c8e870", "bytes": 9912576},
+    "tf32x3": {"kernel_source_sha256_16": "ca06588a475179f0", "bytes": 9939200},
 }
 
 
@@ -474,7 +475,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=32)
-    ap.add_argument("--prec", default="fp32", choices=list(PRECS))
+    ap.add_argument("--prec", default="tf32x3", choices=list(PRECS))
     ap.add_argument("--workload", default="realistic", choices=["realistic", "batched", "serving", "precision", "sigma_eff"])
     ap.add_argument("--controllers", type=int, default=32)
     ap.add_argument("--n-hi", type=int, default=8192, help="serving: largest controller batch N")

@@ -498,6 +498,16 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
 }
 
+// Barrier over the 128 threads of one column group (named barrier `id`);
+// returns whether v was set in any of them.
+__device__ __forceinline__ bool group_sync_or(int id, bool v)
+{
+    uint32_t r;
+    asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, %2, 128, q;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(r) : "r"((uint32_t)v), "r"(id) : "memory");
+    return r != 0;
+}
+
 // Bounded wait on an mbarrier phase; returns false if the limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
 {
@@ -533,31 +543,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
     for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
 
-// This quarter-thread's HQ time steps from tensor memory: 16x128b loads at
-// columns 4k (k < HQ) give thread t lane t/4 and lane t/4 + 8 of column
-// 4k + t%4; `upper` picks the second.  All loads are issued before one wait,
-// and the registers pass through the wait so no use is scheduled before it.
+// Adds to out[k] (k < HQ) this quarter-thread's entries of tensor-memory
+// column col0 + 4k + t%4: a 16x128b load at column col0 + 4k gives thread t
+// lanes t/4 and t/4 + 8; both are added, or the first alone (!both).  Loads
+// are issued four at a time before one wait, and the registers pass through
+// the wait so no use is scheduled before it.
 template <int HQ>
-__device__ __forceinline__ void tmem_ld_quarter(uint32_t taddr, bool upper, float out[HQ])
+__device__ __forceinline__ void tmem_add_quarter(uint32_t taddr, int col0, bool both, float out[HQ])
 {
-    constexpr int G = 4;   // loads per wait
 #pragma unroll
-    for (int k0 = 0; k0 < HQ; k0 += G) {
-        uint32_t lo[G], hi[G];
+    for (int k0 = 0; k0 < HQ; k0 += 4) {
+        uint32_t a[4], c[4];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
+        for (int g = 0; g < 4; ++g) {
+            a[g] = c[g] = 0u;
             if (k0 + g < HQ)
                 asm volatile("tcgen05.ld.sync.aligned.16x128b.x1.b32 {%0, %1}, [%2];"
-                             : "=r"(lo[g]), "=r"(hi[g]) : "r"(taddr + (uint32_t)(4 * (k0 + g))));
-            else
-                lo[g] = hi[g] = 0u;
+                             : "=r"(a[g]), "=r"(c[g]) : "r"(taddr + (uint32_t)(col0 + 4 * (k0 + g))));
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;"
-                     : "+r"(lo[0]), "+r"(hi[0]), "+r"(lo[1]), "+r"(hi[1]), "+r"(lo[2]), "+r"(hi[2]),
-                       "+r"(lo[3]), "+r"(hi[3]) :: "memory");
+                     : "+r"(a[0]), "+r"(c[0]), "+r"(a[1]), "+r"(c[1]), "+r"(a[2]), "+r"(c[2]), "+r"(a[3]), "+r"(c[3])
+                     :: "memory");
 #pragma unroll
-        for (int g = 0; g < G; ++g)
-            if (k0 + g < HQ) out[k0 + g] = __uint_as_float(upper ? hi[g] : lo[g]);
+        for (int g = 0; g < 4; ++g)
+            if (k0 + g < HQ)
+                out[k0 + g] += both ? __uint_as_float(a[g]) + __uint_as_float(c[g]) : __uint_as_float(a[g]);
     }
 }
 
@@ -565,15 +575,18 @@ __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / 
 
 // TC operand sizes.  The reduction (K) runs over the n = H - 1 right-hand-side
 // rows plus one column carrying v0 (so D = K' rhs + kb' v0), padded to the
-// 8-wide MMA granule.  The outputs (N) are the 4*HQ time steps of the four
-// quarters, interleaved (D column 4k + b holds x_{b*HQ + k}) so that one
-// 16x128b tensor-memory load hands each quarter-thread its own time steps.
+// 8-wide MMA granule.  The outputs are the 4*HQ time steps of the four quarters,
+// interleaved (D column 4k + b holds x_{b*HQ + k}) so that one 16x128b
+// tensor-memory load hands each quarter-thread its own time steps, padded to
+// ND rows of B, a multiple of 16 (an M = 128 MMA takes N in steps of 16).
 __host__ __device__ inline int tc_kd(int n) { return round_up(n + 1, 8); }
-__host__ __device__ constexpr int tc_nrows(int hq) { return round_up(4 * hq, 8); }
-// Tensor-memory columns per block: the readback touches columns < 16*ceil(HQ/4).
+__host__ __device__ constexpr int tc_nrows(int hq) { return round_up(4 * hq, 16); }
+// Tensor-memory columns per block: D holds the products with the high parts of
+// B in columns [0, ND) and with the low parts in [ND, 2 ND).
 __host__ __device__ constexpr int tc_tmem_cols(int hq)
 {
-    return round_up(4 * hq, 16) <= 32 ? 32 : round_up(4 * hq, 16) <= 64 ? 64 : round_up(4 * hq, 16) <= 128 ? 128 : 256;
+    return 2 * tc_nrows(hq) <= 32 ? 32 : 2 * tc_nrows(hq) <= 64 ? 64 : 2 * tc_nrows(hq) <= 128 ? 128
+         : 2 * tc_nrows(hq) <= 256 ? 256 : 512;
 }
 
 // ===========================================================================
@@ -624,18 +637,19 @@ __device__ __forceinline__ void normals4(unsigned long long q, unsigned long lon
 // Shared memory: xs[(4HQ+2) x CP] floats (rows x_{-2}, x_{-1}, x_0 ..), rhs
 // [4HQ x CP], kb, wp, v0c, dres; the FP32-pipe variant adds Kt[n x MP]; the
 // tensor-core variant adds the operands A (128 x KD: the tile's right-hand
-// sides and, in column n, v0; tf32 high parts in rows 0..63, remainders in rows
-// 64..127) and B ([K' | kb'] high and low parts, ND x KD each) and keeps D
-// (64 x ND fp32) in tensor memory.  Three MMAs per K-step (A_hi B_hi, A_hi B_lo,
-// A_lo B_hi) accumulate K' rhs + kb' v0 with the products of the two tf32 parts
-// of both operands, i.e. FP32-level accuracy.
+// sides and, in column n, v0, as tf32 high parts and remainders in two rows per
+// column, 64 rows per column group) and B ([K' | kb'] high and low parts, ND x KD
+// each) and keeps one D (64 x ND fp32) per column group in tensor memory.  Two
+// MMAs per K-step (A Bhi, A Blo) give K' rhs + kb' v0 as the sum of the two rows
+// of a column, with the products of the two tf32 parts of both operands, i.e.
+// FP32-level accuracy.
 // ===========================================================================
 template <int HQ>
 __host__ __device__ constexpr int solve_min_blocks() { return HQ <= 17 ? 2 : 1; }
 
 // Shared-memory carve-up of the solve kernel (byte offsets).
 struct SolveSmem {
-    int a, bhi, blo, xs, rhs, kt, kb, wp, v0c, dres, total;
+    int a, bhi, xs, rhs, kt, kb, wp, v0c, dres, total;
 };
 
 __host__ __device__ inline SolveSmem solve_smem(int hq, int n, int MP, bool tc)
@@ -646,16 +660,15 @@ __host__ __device__ inline SolveSmem solve_smem(int hq, int n, int MP, bool tc)
     if (tc) {
         const int KD = tc_kd(n), ND = tc_nrows(hq);
         L.a = off;   off += 128 * KD * 4;
-        L.bhi = off; off += ND * KD * 4;
-        L.blo = off; off += ND * KD * 4;
+        L.bhi = off; off += 2 * ND * KD * 4;   // high parts over low parts (N-stacked)
     } else {
-        L.a = L.bhi = L.blo = 0;
+        L.a = L.bhi = 0;
     }
     L.xs = off;  off += (HP + 2) * CP * 4;   // rows x_{-2} .. x_{HP-1}
     L.rhs = off; off += tc ? 0 : HP * CP * 4;   // SIMT only
     L.kt = off;  off += tc ? 0 : n * MP * 4;
     L.kb = off;  off += MP * 4;
-    L.wp = off;  off += 4 * HP * 4;        // per-row weights: position, velocity, acceleration, jerk
+    L.wp = off;  off += 3 * HP * 4;        // per-row weights: position, acceleration, jerk
     L.v0c = off; off += CMAX * 4;
     L.dres = off; off += CMAX * 4;
     L.total = off;
@@ -680,8 +693,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
     // Per-row weight tables indexed by time: zero on rows that do not exist
     // (jerk row 0, padding rows i >= H), so those rows never reach F^T.
     float *wps = reinterpret_cast<float *>(smem_raw + L.wp);
-    float *wvs = wps + HP;
-    float *was = wvs + HP;
+    float *was = wps + HP;
     float *wjs = was + HP;
     float *v0c = reinterpret_cast<float *>(smem_raw + L.v0c);
     unsigned *dres = reinterpret_cast<unsigned *>(smem_raw + L.dres);
@@ -692,11 +704,14 @@ solve_kernel(const __grid_constant__ LaunchParams P)
     const int c = tid >> 2;       // column in tile
     const int b = tid & 3;        // time quarter
     const int i0 = b * HQ;
-    // Tensor cores: MMA row (A row, D row) of this column, chosen so that the
-    // column's D row sits in a tensor-memory lane this warp can read: the M = 64
-    // accumulator keeps row r in lane 32 (r / 16) + r % 16, warp w reads lanes
-    // 32 (w % 4) .. + 31, and a 16x128b load gives thread t lanes t/4 and t/4 + 8.
-    const int arow = 16 * (warp & 3) + 8 * (warp >> 2) + (lane >> 2);
+    // Tensor cores: one M = 128 MMA per K-step over the whole tile.  Column
+    // 8w + j (warp w, j = lane / 4) keeps the tf32 high parts of its right-hand
+    // side in A row 32 (w % 4) + 16 (w / 4) + j and the remainders 8 rows below.
+    // D row r sits in tensor-memory lane r, which warp w may read (lanes
+    // 32 (w % 4) .. + 31), and one 16x128b load from lane 32 (w % 4) + 16 (w / 4)
+    // hands thread t lanes t/4 and t/4 + 8: both partial products of its column.
+    const int arow_hi = 32 * (warp & 3) + 16 * (warp >> 2) + (lane >> 2);
+    const int arow_lo = arow_hi + 8;
 
     uint32_t tbase = 0, mma_phase = 0;
     if (TC) {
@@ -747,7 +762,6 @@ solve_kernel(const __grid_constant__ LaunchParams P)
             for (int e = tid; e < p.MP; e += NTHREADS) kbs[e] = p.kb[e];
             for (int e = tid; e < HP; e += NTHREADS) {
                 wps[e] = (e < H) ? p.wp[e] : 0.0f;
-                wvs[e] = (e < H) ? p.wv : 0.0f;
                 was[e] = (e < H) ? (e == 0 ? p.wa0 : p.wa) : 0.0f;
                 wjs[e] = (e >= 1 && e < H) ? (e == 1 ? p.wj0 : p.wj) : 0.0f;
             }
@@ -755,14 +769,19 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 // B = [K' | kb'] (rows = D columns in the interleaved output order,
                 // reduction j) split in tf32 high / low parts; A zeroed (its padding
                 // columns k > n must stay zero).
-                for (int e = tid; e < ND * KD; e += NTHREADS) {
+                // Rows [0, ND) of the N-stacked operand hold the high parts, rows
+                // [ND, 2 ND) the low parts, laid out with this problem's KD (the
+                // region is sized for the launch's largest).
+                for (int e = tid; e < 2 * ND * KD; e += NTHREADS) {
                     const int pr = e / KD, j = e - pr * KD;
-                    const int xt = (pr & 3) * HQ + (pr >> 2);   // time step of D column pr
+                    const bool low = pr >= ND;
+                    const int pc = low ? pr - ND : pr;
+                    const int xt = (pc & 3) * HQ + (pc >> 2);   // time step of D column pc
                     const int i = xt - 1;                       // its row of [K' | kb']
                     const bool in = xt >= 1 && xt <= n && j <= n;   // column n: kb'
                     const int src = i * (n + 1) + j;
-                    *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, j, KD)) = in ? p.Khi[src] : 0.0f;
-                    *reinterpret_cast<float *>(smem_raw + L.blo + cm_off(pr, j, KD)) = in ? p.Klo[src] : 0.0f;
+                    *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, j, KD)) =
+                        in ? (low ? p.Klo[src] : p.Khi[src]) : 0.0f;
                 }
                 for (int e = tid; e < 128 * KD; e += NTHREADS) reinterpret_cast<float *>(As)[e] = 0.0f;
             }
@@ -828,8 +847,8 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 // column n of A: v0 of this column, split like the right-hand sides
                 const float v = colv ? v0j : 0.0f;
                 const float hi = tf32_rna(v);
-                *reinterpret_cast<float *>(As + cm_off(arow, n, KD)) = hi;
-                *reinterpret_cast<float *>(As + 64 * KD * 4 + cm_off(arow, n, KD)) = v - hi;
+                *reinterpret_cast<float *>(As + cm_off(arow_hi, n, KD)) = hi;
+                *reinterpret_cast<float *>(As + cm_off(arow_lo, n, KD)) = v - hi;
             }
         }
         __syncthreads();
@@ -876,6 +895,14 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 }
             }
         }
+        if (TC) {
+            // the iteration keeps x in registers, so the tile holds xi instead
+            // (13-33 registers fewer in the loop)
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) xs[(i0 + r + 2) * CP + c] = xi[r];
+            __syncthreads();
+        }
 
         for (int l = 0; l < iters; ++l) {
             // ---- stencil phase: a3 slack / clip, a4 Fh^T, a6 multiplier -> rhs
@@ -884,7 +911,9 @@ solve_kernel(const __grid_constant__ LaunchParams P)
             float g[HQ], rv[HQ];
             // Rows that do not exist carry zero weight, so their multiplier state may
             // drift freely (it stays finite: the drift per iteration is bounded by
-            // the row's own violation) without reaching the iterate.  The acceleration
+            // the row's own violation) without reaching the iterate.  Velocity rows
+            // keep the uniform weight: one reaches F^T only at its own time step,
+            // whose right-hand side is never used when the row does not exist.  The acceleration
             // row k=1 and the first jerk row (k=2) have shifted bounds; they only
             // occur in quarter 0 at r = 0 and r = 1, so the test is compile-time for r >= 2.
             if (MODE == PRISM_MODE_ADMM) {
@@ -900,7 +929,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     float z;
                     z = clampf(2.0f * yv - t_v[r], cb.vlo, cb.vhi);
                     t_v[r] = (z - yv) + t_v[r];
-                    s.v[r] = wvs[i] * t_v[r];
+                    s.v[r] = wv * t_v[r];
                     z = clampf(2.0f * yp - t_p[r], cb.plo, cb.phi);
                     t_p[r] = (z - yp) + t_p[r];
                     s.p[r] = wps[i] * t_p[r];
@@ -913,7 +942,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 }
                 apply_FT<HQ>(s, b, g);
 #pragma unroll
-                for (int r = 0; r < HQ; ++r) rv[r] = fmaf(rho, g[r], xi[r]);
+                for (int r = 0; r < HQ; ++r) rv[r] = fmaf(rho, g[r], TC ? xs[(i0 + r + 2) * CP + c] : xi[r]);
             } else {
                 if (l > 0) {   // complete lambda <- lambda~ - rho Fh^T W y^l
                     float cs = X.pre;
@@ -923,7 +952,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                         cs += X.w[r + 2];
                         const float ya = X.w[r + 2] - X.w[r + 1];
                         const float yj = ya - (X.w[r + 1] - X.w[r]);
-                        s.v[r] = wvs[i] * X.w[r + 2];
+                        s.v[r] = wv * X.w[r + 2];
                         s.p[r] = wps[i] * cs;
                         s.a[r] = was[i] * ya;
                         s.j[r] = wjs[i] * yj;
@@ -945,7 +974,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     const float pp = yp + clampf(yp, cb.plo, cb.phi);
                     const float pa = ya + (f0 ? clampf(ya, cb.alo0, cb.ahi0) : clampf(ya, cb.alo, cb.ahi));
                     const float pj = yj + (f1 ? clampf(yj, cb.jlo1, cb.jhi1) : clampf(yj, cb.jlo, cb.jhi));
-                    s.v[r] = wvs[i] * pv;
+                    s.v[r] = wv * pv;
                     s.p[r] = wps[i] * pp;
                     s.a[r] = was[i] * pa;
                     s.j[r] = wjs[i] * pj;
@@ -953,7 +982,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 apply_FT<HQ>(s, b, g);
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
-                    rv[r] = fmaf(rho, g[r], lam[r] + xi[r]);
+                    rv[r] = fmaf(rho, g[r], lam[r] + (TC ? xs[(i0 + r + 2) * CP + c] : xi[r]));
                     lam[r] = fmaf(0.5f * rho, g[r], lam[r]);
                 }
             }
@@ -968,48 +997,42 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 kapply(xs, rhs, Kts, kbs, v0c, dres, n, p.MP, CP, ncg, last);
                 __syncthreads();
             } else {
-                // rhs -> A_hi (tf32 high parts) and A_lo (remainders) in this column's
-                // MMA row, K = i - 1.  Iterations before the polish phase use the high
-                // parts only.
+                // rhs -> tf32 high parts and remainders in this column's two A rows,
+                // K = i - 1.  Iterations before the polish phase use the high parts only.
                 const bool split = l >= iters - polish;
-                const int a_lo = 64 * KD * 4;   // byte offset of A_lo after A_hi
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
                     const int i = i0 + r;
                     if (i >= 1 && i < H) {
                         const float hi = tf32_rna(rv[r]);
-                        *reinterpret_cast<float *>(As + cm_off(arow, i - 1, KD)) = hi;
-                        if (split) *reinterpret_cast<float *>(As + a_lo + cm_off(arow, i - 1, KD)) = rv[r] - hi;
+                        *reinterpret_cast<float *>(As + cm_off(arow_hi, i - 1, KD)) = hi;
+                        if (split) *reinterpret_cast<float *>(As + cm_off(arow_lo, i - 1, KD)) = rv[r] - hi;
                     }
                 }
                 // A visible to the tensor core, the previous readback of D finished;
-                // a warp whose MMA wait ran out stops the whole block here
+                // a warp whose MMA wait ran out stops the block here
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 if (__syncthreads_or(timed_out)) {
-                    if (tid == 0 && p.err) atomicExch(p.err, 1);
                     aborted = true;
                     break;
                 }
-                // ---- a5: K-apply on the tensor cores, one M=64 accumulator:
-                // D[row][col] = sum_j (A_hi Bhi + A_hi Blo + A_lo Bhi), j over the
-                // right-hand-side rows and the v0 column, B = [K' | kb'] in the
-                // interleaved output order
+                // ---- a5: K-apply on the tensor cores, one M=128 MMA per K-step:
+                // D[row][col] = sum_j A[row][j] B[col][j], j over the right-hand-side
+                // rows and the v0 column, B = [K' | kb'] high parts (columns < ND, in
+                // the interleaved output order) stacked over its low parts (columns
+                // >= ND; only in the polish phase)
                 if (tid == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t idesc = umma_idesc_tf32(64, ND);
-                    const uint32_t ah = smem_addr(As), al = ah + (uint32_t)a_lo;
-                    const uint32_t bh = smem_addr(smem_raw + L.bhi), bl = smem_addr(smem_raw + L.blo);
+                    const uint32_t idesc = umma_idesc_tf32(128, split ? 2 * ND : ND);
                     const uint32_t sbo = (uint32_t)(KD >> 2) * 128u;
+                    const uint64_t da = umma_desc(smem_addr(As), 128u, sbo);
+                    const uint64_t db = umma_desc(smem_addr(smem_raw + L.bhi), 128u, sbo);
                     for (int ks = 0; ks < (KD >> 3); ++ks) {
-                        const uint32_t koff = (uint32_t)ks * 256u;
-                        const uint64_t adh = umma_desc(ah + koff, 128u, sbo);
-                        const uint64_t bdh = umma_desc(bh + koff, 128u, sbo);
-                        umma_tf32(tbase, adh, bdh, idesc, ks > 0 ? 1u : 0u);
-                        if (split) {
-                            umma_tf32(tbase, adh, umma_desc(bl + koff, 128u, sbo), idesc, 1u);
-                            umma_tf32(tbase, umma_desc(al + koff, 128u, sbo), bdh, idesc, 1u);
-                        }
+                        // the descriptor's address field counts 16-byte units: a K-step
+                        // (two 128-byte core matrices) is 16 of them
+                        const uint64_t kk = (uint64_t)(16 * ks);
+                        umma_tf32(tbase, da + kk, db + kk, idesc, ks > 0 ? 1u : 0u);
                     }
                     umma_commit(smem_addr(&mma_bar));
                 }
@@ -1021,13 +1044,17 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     timed_out = true;   // X keeps the old iterate; the block stops at the next barrier
                 } else {
                     // readback straight into the x window: D column 4k + b holds
-                    // x_{b*HQ + k}; lane t/4 (warps 0-3) or t/4 + 8 (warps 4-7) is
-                    // this thread's column
+                    // x_{b*HQ + k} (products with the high parts of B), column ND + 4k + b
+                    // the products with its low parts; outside the polish phase only
+                    // the high rows and high parts count (the remainder rows of A
+                    // are not rewritten then)
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t tl = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
-                    const bool upper = warp >= 4;
+                    const uint32_t tl = tbase + ((uint32_t)(32 * (warp & 3) + 16 * (warp >> 2)) << 16);
                     float xn[HQ];
-                    tmem_ld_quarter<HQ>(tl, upper, xn);
+#pragma unroll
+                    for (int r = 0; r < HQ; ++r) xn[r] = 0.0f;
+                    tmem_add_quarter<HQ>(tl, 0, split, xn);
+                    if (split) tmem_add_quarter<HQ>(tl, ND, true, xn);
                     if (b == 0) xn[0] = colv ? v0j : 0.0f;   // x_0 = v0 exactly
                     if (last) {
                         float dm = 0.0f;
@@ -1044,8 +1071,8 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 }
             }
         }
-        if (TC && !aborted) {
-            if (__syncthreads_or(timed_out)) {
+        if (TC) {
+            if (__syncthreads_or(aborted || timed_out)) {
                 if (tid == 0 && p.err) atomicExch(p.err, 1);
                 aborted = true;
             }
@@ -1398,7 +1425,7 @@ bool tc_fits(int H)
     const Variant *v = pick_variant(H);
     if (!v) return false;
     const int n = H - 1;
-    return solve_smem(v->hq, n, (n + 3) & ~3, true).total <= 220 * 1024 && tc_nrows(v->hq) <= 256;
+    return solve_smem(v->hq, n, (n + 3) & ~3, true).total <= 220 * 1024 && 2 * tc_nrows(v->hq) <= 256;
 }
 
 bool is_finite(double v) { return std::isfinite(v); }
@@ -1487,6 +1514,8 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
     const int own = std::min(std::min((int)(smem_sm / per_block), regs_sm / std::max(1, fa.numRegs * NTHREADS)),
                              2048 / NTHREADS);
     blocks_per_sm = std::max(blocks_per_sm, own);
+    // each resident block holds its accumulator in the SM's 512 tensor-memory columns
+    if (tc) blocks_per_sm = std::min(blocks_per_sm, 512 / tc_tmem_cols(v->hq));
     if (blocks_per_sm < 1) return fail(PRISM_ERR_UNSUPPORTED, "solve kernel does not fit on an SM (smem %zu)", smem);
     return PRISM_OK;
 }

@@ -163,7 +163,7 @@ struct Server {
     std::string last_error;
 
     void run();
-    void launch(const std::shared_ptr<Request> &r, int slot);
+    bool enqueue(const std::shared_ptr<Request> &r, const Controller &c, bool warm_in);
     void retire(int slot);
 };
 
@@ -185,10 +185,13 @@ void CUDART_CB on_request_done(void *arg)
 
 }  // namespace
 
-void Server::launch(const std::shared_ptr<Request> &r, int slot)
+// Enqueues one admitted request on its slot's stream: input copies, the
+// warm-start shift, the solve, the result copies and the completion callback.
+// Runs on the scheduler thread WITHOUT the server lock (a copy into pageable
+// host memory blocks until the solve ends), on a snapshot of the controller.
+bool Server::enqueue(const std::shared_ptr<Request> &r, const Controller &c, bool warm_in)
 {
-    Controller &c = ctrls[r->ctrl];
-    cudaStream_t s = streams[slot];
+    cudaStream_t s = streams[r->slot];
     char *base = arena.base + r->off;
     const size_t seq = (size_t)c.N * c.H * c.J;
     float *d_xi = reinterpret_cast<float *>(base);
@@ -200,10 +203,10 @@ void Server::launch(const std::shared_ptr<Request> &r, int slot)
     bool ok = cudaMemcpyAsync(d_xi, r->xi, seq * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(d_q0, r->q0, c.J * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(d_v0, r->v0, c.J * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess;
-    if (ok && c.warm && c.has_state) ok = prism_proj_shift_state(c.h, c.N, 1, nullptr, d_state, s) == PRISM_OK;
+    if (ok && warm_in) ok = prism_proj_shift_state(c.h, c.N, 1, nullptr, d_state, s) == PRISM_OK;
     prism_solve_opts o;
     o.x_init = nullptr;
-    o.dual_init = (c.warm && c.has_state) ? d_state : nullptr;
+    o.dual_init = warm_in ? d_state : nullptr;
     o.dual_out = c.warm ? d_state : nullptr;
     o.polish_iters = 0;
     if (ok)
@@ -214,19 +217,8 @@ void Server::launch(const std::shared_ptr<Request> &r, int slot)
         ok = cudaMemcpyAsync(r->primal, d_pr, (size_t)c.N * c.J * sizeof(float), cudaMemcpyDeviceToHost, s) ==
              cudaSuccess;
     if (ok) ok = cudaLaunchHostFunc(s, on_request_done, r.get()) == cudaSuccess;
-    r->slot = slot;
-    slot_req[slot] = r;
-    c.busy = true;
-    if (!ok) {
-        last_error = prism_last_error();
-        // wait for whatever was enqueued, then report the failure
-        cudaStreamSynchronize(s);
-        r->state.store(Q_FAILED);
-        r->t_done = now_s();
-    } else {
-        r->state.store(Q_RUNNING);
-        if (c.warm) c.has_state = true;
-    }
+    if (!ok) cudaStreamSynchronize(s);   // let whatever was enqueued finish before the buffers are reused
+    return ok;
 }
 
 void Server::retire(int slot)
@@ -255,6 +247,12 @@ void Server::run()
 {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
+    struct Job {
+        std::shared_ptr<Request> r;
+        Controller c;      // snapshot: the controller list may grow while unlocked
+        bool warm_in;
+    };
+    std::vector<Job> jobs;
     while (!stop) {
         // retire finished requests
         for (size_t k = 0; k < slot_req.size(); ++k)
@@ -275,9 +273,39 @@ void Server::run()
             if (!arena.alloc(bytes, off)) { ++it; continue; }   // wait for memory to free up
             r->off = off;
             r->bytes = bytes;
+            r->slot = slot;
             if (c.queued == r) c.queued.reset();
             it = fifo.erase(it);
-            launch(r, slot);
+            slot_req[slot] = r;
+            c.busy = true;
+            r->state.store(Q_RUNNING);
+            Job j;
+            j.r = r;
+            j.c = c;
+            j.c.queued.reset();
+            j.warm_in = c.warm && c.has_state;
+            jobs.push_back(std::move(j));
+        }
+        if (!jobs.empty()) {
+            // enqueue outside the lock: submitters and waiters are never held up
+            // by the copies (which block for pageable host buffers)
+            lk.unlock();
+            std::vector<bool> ok(jobs.size());
+            for (size_t k = 0; k < jobs.size(); ++k) ok[k] = enqueue(jobs[k].r, jobs[k].c, jobs[k].warm_in);
+            std::string err = prism_last_error();
+            lk.lock();
+            for (size_t k = 0; k < jobs.size(); ++k) {
+                Request &r = *jobs[k].r;
+                if (ok[k]) {
+                    if (jobs[k].c.warm) ctrls[r.ctrl].has_state = true;
+                } else {
+                    last_error = err;
+                    r.t_done = now_s();
+                    r.state.store(Q_FAILED);
+                }
+            }
+            jobs.clear();
+            continue;   // retire what finished meanwhile before sleeping
         }
         cv.wait_for(lk, std::chrono::microseconds(200));
     }

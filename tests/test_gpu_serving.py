@@ -101,7 +101,7 @@ def test_admission_and_supersede():
     assert e.value.status == 5
     small.close()
     S = pp.Server(mem_budget_bytes=1 << 28, max_inflight=1)
-    cid = S.add_controller(P, N, 20000, warm=True)      # ~0.1 s per request
+    cid = S.add_controller(P, N, 100000, warm=True)     # tens of ms or more per request
     b = workloads.make_custom(5, N, J, H, dt)
     outs = [np.empty((N, H, J), np.float32) for _ in range(3)]
     t0 = S.submit(cid, b["q0"], b["v0"], b["xi"], outs[0])
