@@ -498,14 +498,12 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
 }
 
-// Barrier over the 128 threads of one column group (named barrier `id`);
-// returns whether v was set in any of them.
-__device__ __forceinline__ bool group_sync_or(int id, bool v)
+// One lane of the (converged) warp.
+__device__ __forceinline__ bool elect_one()
 {
-    uint32_t r;
-    asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, %2, 128, q;\nselp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(r) : "r"((uint32_t)v), "r"(id) : "memory");
-    return r != 0;
+    uint32_t pred = 0;
+    asm volatile("{\n.reg .pred P;\nelect.sync _|P, 0xffffffff;\nselp.u32 %0, 1, 0, P;\n}\n" : "=r"(pred));
+    return pred != 0;
 }
 
 // Bounded wait on an mbarrier phase; returns false if the limit ran out.
@@ -578,9 +576,10 @@ __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / 
 // 8-wide MMA granule.  The outputs are the 4*HQ time steps of the four quarters,
 // interleaved (D column 4k + b holds x_{b*HQ + k}) so that one 16x128b
 // tensor-memory load hands each quarter-thread its own time steps, padded to
-// ND rows of B, a multiple of 16 (an M = 128 MMA takes N in steps of 16).
+// ND = 4*HQ + 4 rows of B (HQ is odd), so that the N-stacked operand (2 ND rows)
+// suits an M = 128 MMA, which takes N in steps of 16.
 __host__ __device__ inline int tc_kd(int n) { return round_up(n + 1, 8); }
-__host__ __device__ constexpr int tc_nrows(int hq) { return round_up(4 * hq, 16); }
+__host__ __device__ constexpr int tc_nrows(int hq) { return round_up(4 * hq, 8); }
 // Tensor-memory columns per block: D holds the products with the high parts of
 // B in columns [0, ND) and with the low parts in [ND, 2 ND).
 __host__ __device__ constexpr int tc_tmem_cols(int hq)
@@ -1022,19 +1021,27 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 // rows and the v0 column, B = [K' | kb'] high parts (columns < ND, in
                 // the interleaved output order) stacked over its low parts (columns
                 // >= ND; only in the polish phase)
-                if (tid == 0) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t idesc = umma_idesc_tf32(128, split ? 2 * ND : ND);
+                if (warp == 0) {
+                    // descriptors formed by the whole warp (uniform), one elected lane
+                    // issues (measured: about 25 % less issue time than forming them in
+                    // a single thread)
+                    // without the low parts the MMA still spans a multiple of 16 rows of
+                    // B; columns >= ND of D are then not read
+                    const uint32_t idesc = umma_idesc_tf32(128, split ? 2 * ND : round_up(ND, 16));
                     const uint32_t sbo = (uint32_t)(KD >> 2) * 128u;
                     const uint64_t da = umma_desc(smem_addr(As), 128u, sbo);
                     const uint64_t db = umma_desc(smem_addr(smem_raw + L.bhi), 128u, sbo);
-                    for (int ks = 0; ks < (KD >> 3); ++ks) {
-                        // the descriptor's address field counts 16-byte units: a K-step
-                        // (two 128-byte core matrices) is 16 of them
-                        const uint64_t kk = (uint64_t)(16 * ks);
-                        umma_tf32(tbase, da + kk, db + kk, idesc, ks > 0 ? 1u : 0u);
+                    if (elect_one()) {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        for (int ks = 0; ks < (KD >> 3); ++ks) {
+                            // the descriptor's address field counts 16-byte units: a K-step
+                            // (two 128-byte core matrices) is 16 of them
+                            const uint64_t kk = (uint64_t)(16 * ks);
+                            umma_tf32(tbase, da + kk, db + kk, idesc, ks > 0 ? 1u : 0u);
+                        }
+                        umma_commit(smem_addr(&mma_bar));
                     }
-                    umma_commit(smem_addr(&mma_bar));
+                    __syncwarp();
                 }
                 // every warp polls the mbarrier (measured: letting one warp poll and the
                 // others sleep in the block barrier made the iteration 1.6x slower)
