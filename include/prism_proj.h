@@ -70,7 +70,10 @@ typedef enum {
     PRISM_ERR_INFEASIBLE_BOUNDS = 4,/* bounds that admit no trajectory                */
     PRISM_ERR_OOM = 5,              /* device or host allocation failed               */
     PRISM_ERR_CUDA = 6,             /* a CUDA runtime call failed (text in last_error) */
-    PRISM_ERR_UNSUPPORTED = 7       /* valid request this build does not implement    */
+    PRISM_ERR_UNSUPPORTED = 7,      /* valid request this build does not implement    */
+    PRISM_ERR_TIMEOUT = 8           /* a bounded device-side wait ran out: the results
+                                       of that launch are invalid (see
+                                       prism_proj_device_status)                      */
 } prism_status;
 
 enum { PRISM_MODE_ADMM = 0, PRISM_MODE_PAPER = 1 };
@@ -203,6 +206,7 @@ prism_status prism_proj_solve_plain(prism_proj_t h, int batch, const float *q0, 
  * fastest copies) to device staging buffers owned by the handle, runs
  * prism_proj_solve, copies x (and the residuals when the pointers are not
  * NULL) back to host memory, and synchronises cuda_stream before returning.
+ * A device-side wait that ran out during the solve returns PRISM_ERR_TIMEOUT.
  */
 prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_host,
                                    const float *v0_host, const float *samples_host, int iters,
@@ -394,6 +398,28 @@ size_t prism_mppi_workspace_bytes(int N, int H, int J);
 prism_status prism_mppi_update(int N, int H, int J, const float *cost, double temperature, double eps,
                                const float *x, float *mean, float *var, float *weights, void *workspace,
                                size_t workspace_bytes, void *cuda_stream);
+
+/*
+ * prism_proj_device_status -- device-side errors of this handle's launches.
+ * The tensor-core solve waits for its MMAs with a bounded poll (about a second
+ * at most); when a bound runs out, the launch stops early, leaves its outputs
+ * invalid and raises a flag in device memory.  This call synchronises
+ * cuda_stream, reads and clears that flag and returns PRISM_ERR_TIMEOUT if any
+ * launch of the handle since the previous call timed out, else PRISM_OK.  The
+ * CUDA context stays usable after a timeout.
+ */
+prism_status prism_proj_device_status(prism_proj_t h, void *cuda_stream);
+
+/*
+ * prism_diag_wait_timeout -- self-test of the bounded device-side wait (the
+ * paper has no counterpart).  One block waits on an mbarrier phase that
+ * nothing completes, polling at most poll_limit times (1 .. 2^22) with the
+ * same routine the tensor-core solve uses; *timed_out receives 1 when the
+ * bound ran out (the expected outcome) and 0 if the phase completed.  Runs on
+ * the current device's default stream and synchronises it; allocates (and
+ * frees) one int of device memory.
+ */
+prism_status prism_diag_wait_timeout(unsigned int poll_limit, int *timed_out);
 
 /* prism_proj_destroy -- free the handle and its device memory (synchronises the device). */
 prism_status prism_proj_destroy(prism_proj_t h);

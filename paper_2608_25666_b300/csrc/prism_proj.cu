@@ -507,10 +507,10 @@ __device__ __forceinline__ bool elect_one()
 }
 
 // Bounded wait on an mbarrier phase; returns false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit = 1u << 22)
 {
     uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it)
+    for (uint32_t it = 0; it < limit && !done; ++it)
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
     return done != 0;
@@ -570,6 +570,20 @@ __device__ __forceinline__ void tmem_add_quarter(uint32_t taddr, int col0, bool 
 }
 
 __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Self-test of the bounded wait: a phase that nothing completes.  flag = 1 when
+// the bound ran out, 0 if the phase completed.
+__global__ void diag_wait_kernel(uint32_t limit, int *flag)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool done = mbar_wait(smem_addr(&bar), 0u, limit);
+    if (threadIdx.x == 0) *flag = done ? 0 : 1;
+}
 
 // TC operand sizes.  The reduction (K) runs over the n = H - 1 right-hand-side
 // rows plus one column carrying v0 (so D = K' rhs + kb' v0), padded to the
@@ -1683,6 +1697,7 @@ const char *prism_status_string(prism_status s)
     case PRISM_ERR_OOM: return "PRISM_ERR_OOM";
     case PRISM_ERR_CUDA: return "PRISM_ERR_CUDA";
     case PRISM_ERR_UNSUPPORTED: return "PRISM_ERR_UNSUPPORTED";
+    case PRISM_ERR_TIMEOUT: return "PRISM_ERR_TIMEOUT";
     }
     return "PRISM_ERR_UNKNOWN";
 }
@@ -1983,7 +1998,40 @@ prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_ho
     CUDA_TRY(cudaMemcpyAsync(out_host, d_x, sizeof(float) * seq, cudaMemcpyDeviceToHost, s));
     if (primal_res_host) CUDA_TRY(cudaMemcpyAsync(primal_res_host, d_pr, sizeof(float) * cols, cudaMemcpyDeviceToHost, s));
     if (dual_res_host) CUDA_TRY(cudaMemcpyAsync(dual_res_host, d_du, sizeof(float) * cols, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    return prism_proj_device_status(h, cuda_stream);
+}
+
+prism_status prism_proj_device_status(prism_proj_t h, void *cuda_stream)
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    if (!h->d_err) return PRISM_OK;   // not factored yet: nothing has run
+    int flag = 0;
+    CUDA_TRY(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!flag) return PRISM_OK;
+    CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+    return fail(PRISM_ERR_TIMEOUT, "a device-side wait of a solve on this handle ran out its bound");
+}
+
+prism_status prism_diag_wait_timeout(unsigned int poll_limit, int *timed_out)
+{
+    if (!timed_out) return fail(PRISM_ERR_INVALID_ARG, "timed_out is NULL");
+    if (poll_limit < 1 || poll_limit > (1u << 22)) return fail(PRISM_ERR_INVALID_ARG, "poll_limit outside [1, 2^22]");
+    *timed_out = -1;
+    int *d_flag = nullptr;
+    CUDA_TRY(cudaMalloc(&d_flag, sizeof(int)));
+    cudaError_t e = cudaMemset(d_flag, 0xff, sizeof(int));
+    if (e == cudaSuccess) {
+        diag_wait_kernel<<<1, 32>>>(poll_limit, d_flag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int flag = -1;
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d_flag);
+    if (e != cudaSuccess) return fail(PRISM_ERR_CUDA, "wait self-test: %s", cudaGetErrorString(e));
+    *timed_out = flag;
     return PRISM_OK;
 }
 

@@ -25,7 +25,7 @@ MAX_H, MAX_J = 132, 64
 
 STATUS = {0: "PRISM_OK", 1: "PRISM_ERR_INVALID_ARG", 2: "PRISM_ERR_NOT_FACTORED",
           3: "PRISM_ERR_RHO_MISMATCH", 4: "PRISM_ERR_INFEASIBLE_BOUNDS", 5: "PRISM_ERR_OOM",
-          6: "PRISM_ERR_CUDA", 7: "PRISM_ERR_UNSUPPORTED"}
+          6: "PRISM_ERR_CUDA", 7: "PRISM_ERR_UNSUPPORTED", 8: "PRISM_ERR_TIMEOUT"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libprism_proj.so")
@@ -81,8 +81,11 @@ def lib() -> ctypes.CDLL:
             L.prism_proj_get_factor.argtypes = [P, P, P]
             L.prism_proj_query.argtypes = [P, i, ctypes.POINTER(ll)]
             L.prism_proj_destroy.argtypes = [P]
+            L.prism_proj_device_status.argtypes = [P, P]
+            L.prism_diag_wait_timeout.argtypes = [ctypes.c_uint, ctypes.POINTER(i)]
+            L.prism_diag_wait_timeout.restype = i
             for name in ("create", "factor", "solve", "solve_ex", "solve_plain", "solve_host",
-                         "check_fp64", "shift_state", "get_factor", "query", "destroy"):
+                         "check_fp64", "shift_state", "get_factor", "query", "device_status", "destroy"):
                 getattr(L, "prism_proj_" + name).restype = i
             L.prism_plan_create.argtypes = [P, i, i, i, ctypes.POINTER(P)]
             L.prism_plan_launch.argtypes = [P, P]
@@ -295,6 +298,11 @@ class Projector:
         _check(lib().prism_proj_shift_state(self._h, N, int(steps), _ptr(x), _ptr(dual),
                                             _stream_ptr(stream)))
 
+    def device_status(self, stream=None):
+        """prism_proj_device_status: synchronise ``stream`` and raise PrismError
+        (PRISM_ERR_TIMEOUT) if a launch of this handle hit a device-side wait bound."""
+        _check(lib().prism_proj_device_status(self._h, _stream_ptr(stream)))
+
     def check_fp64(self, q0, v0, x, stream=None):
         """prism_proj_check_fp64: FP64 primal residual [N, J] (CUDA float64 tensor)."""
         import torch
@@ -457,6 +465,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def diag_wait_timeout(poll_limit: int = 1000) -> bool:
+    """prism_diag_wait_timeout: run the bounded device wait on a phase that nothing
+    completes; True when the bound ran out (the expected outcome)."""
+    flag = ctypes.c_int(-1)
+    _check(lib().prism_diag_wait_timeout(int(poll_limit), ctypes.byref(flag)))
+    return flag.value == 1
 
 
 def mppi_update(cost, x, temperature: float, eps: float = 0.0, workspace=None, stream=None):

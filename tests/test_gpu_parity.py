@@ -191,6 +191,27 @@ def test_errors_are_reported_not_raised_on_device():
     P.close()
 
 
+def test_bounded_wait_times_out_and_the_context_survives():
+    """The bounded device-side wait (the one the tensor-core solve uses for its
+    MMAs) on a phase that nothing completes runs out, reports it, and the next
+    solves still run and match the oracle; a clean handle reports no timeout."""
+    assert pp.diag_wait_timeout(1000) is True
+    assert pp.diag_wait_timeout(20000) is True
+    b = workloads.make_custom(13, 6, 5, 21, 0.05)
+    g = gpu_solve(b, 30, 1.0, prec=pp.PREC_TF32X3)
+    o = oracle_solve(b, 30, 1.0)
+    assert_parity(g, o, dual_tol=2e-4)
+    P = pp.Projector(5, 21, 0.05, b["bounds"]).factor(1.0, prec=pp.PREC_TF32X3)
+    xi, q0, v0 = to_dev(b)
+    P.solve(q0, v0, xi, 30)
+    P.device_status()          # raises PrismError(PRISM_ERR_TIMEOUT) if a wait ran out
+    P.close()
+    with pytest.raises(pp.PrismError) as e:
+        lib_status = pp.lib().prism_diag_wait_timeout(0, None)
+        pp._check(lib_status)
+    assert e.value.status == 1
+
+
 def test_unscaled_rows_fp32_error_is_reported():
     """Printed (unscaled) rows: the FP32 iteration is ill-conditioned; the
     error against the oracle is measured, not gated at 1e-4."""
