@@ -585,14 +585,19 @@ __global__ void diag_wait_kernel(uint32_t limit, int *flag)
     if (threadIdx.x == 0) *flag = done ? 0 : 1;
 }
 
-// TC operand sizes.  The reduction (K) runs over the n = H - 1 right-hand-side
-// rows plus one column carrying v0 (so D = K' rhs + kb' v0), padded to the
-// 8-wide MMA granule.  The outputs are the 4*HQ time steps of the four quarters,
-// interleaved (D column 4k + b holds x_{b*HQ + k}) so that one 16x128b
-// tensor-memory load hands each quarter-thread its own time steps, padded to
-// ND = 4*HQ + 4 rows of B (HQ is odd), so that the N-stacked operand (2 ND rows)
-// suits an M = 128 MMA, which takes N in steps of 16.
-__host__ __device__ inline int tc_kd(int n) { return round_up(n + 1, 8); }
+// TC operand sizes.  The reduction (K) gives each quarter a block of HQ4 =
+// HQ rounded up to 4 indices: K index HQ4*b + r is time step b*HQ + r (r < HQ),
+// so a quarter-thread's right-hand-side rows sit at compile-time offsets from
+// its block and an MMA K-step sums consecutive time steps (the tensor core's
+// internal accumulation is then as accurate as in time order); index HQ (the
+// first spare slot of quarter 0) carries v0, so D = K' rhs + kb' v0; entries of
+// B for time steps that are not right-hand-side rows (x_0, padding) are zero.
+// The outputs (N) are interleaved: D column 4k + b holds x_{b*HQ + k}, so one
+// 16x128b tensor-memory load hands each quarter-thread its own time steps,
+// padded to ND = 4*HQ + 4 rows of B (HQ is odd), so that the N-stacked operand
+// (2 ND rows) suits an M = 128 MMA (N in steps of 16).
+__host__ __device__ constexpr int tc_hq4(int hq) { return round_up(hq, 4); }
+__host__ __device__ constexpr int tc_kd(int hq) { return 4 * tc_hq4(hq); }
 __host__ __device__ constexpr int tc_nrows(int hq) { return round_up(4 * hq, 8); }
 // Tensor-memory columns per block: D holds the products with the high parts of
 // B in columns [0, ND) and with the low parts in [ND, 2 ND).
@@ -671,7 +676,7 @@ __host__ __device__ inline SolveSmem solve_smem(int hq, int n, int MP, bool tc)
     SolveSmem L;
     int off = 0;
     if (tc) {
-        const int KD = tc_kd(n), ND = tc_nrows(hq);
+        const int KD = tc_kd(hq), ND = tc_nrows(hq);
         L.a = off;   off += 128 * KD * 4;
         L.bhi = off; off += 2 * ND * KD * 4;   // high parts over low parts (N-stacked)
     } else {
@@ -762,7 +767,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
         const float rho = p.rho;
         const float wv = p.wv, wa0 = p.wa0, wa = p.wa, wj0 = p.wj0, wj = p.wj;
         const int iters = p.iters, polish = p.polish;
-        const int KD = tc_kd(n), ND = tc_nrows(HQ);
+        constexpr int KD = tc_kd(HQ), ND = tc_nrows(HQ);
         const int n0 = (tile - p.tile0) * p.T;
         const int Tt = min(p.T, p.N - n0);
         const int Ct = Tt * J;
@@ -786,14 +791,19 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 // [ND, 2 ND) the low parts, laid out with this problem's KD (the
                 // region is sized for the launch's largest).
                 for (int e = tid; e < 2 * ND * KD; e += NTHREADS) {
-                    const int pr = e / KD, j = e - pr * KD;
+                    const int pr = e / KD, kq = e - pr * KD;
                     const bool low = pr >= ND;
                     const int pc = low ? pr - ND : pr;
                     const int xt = (pc & 3) * HQ + (pc >> 2);   // time step of D column pc
                     const int i = xt - 1;                       // its row of [K' | kb']
-                    const bool in = xt >= 1 && xt <= n && j <= n;   // column n: kb'
+                    constexpr int HQ4 = tc_hq4(HQ);
+                    const int kb_ = kq / HQ4, kr = kq - kb_ * HQ4;
+                    const int xk = kb_ * HQ + kr;               // time step of K index kq
+                    const bool v0col = kq == HQ;
+                    const int j = v0col ? n : xk - 1;           // its column of [K' | kb']
+                    const bool in = xt >= 1 && xt <= n && (v0col || (kr < HQ && xk >= 1 && xk <= n));
                     const int src = i * (n + 1) + j;
-                    *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, j, KD)) =
+                    *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, kq, KD)) =
                         in ? (low ? p.Klo[src] : p.Khi[src]) : 0.0f;
                 }
                 for (int e = tid; e < 128 * KD; e += NTHREADS) reinterpret_cast<float *>(As)[e] = 0.0f;
@@ -860,8 +870,8 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 // column n of A: v0 of this column, split like the right-hand sides
                 const float v = colv ? v0j : 0.0f;
                 const float hi = tf32_rna(v);
-                *reinterpret_cast<float *>(As + cm_off(arow_hi, n, KD)) = hi;
-                *reinterpret_cast<float *>(As + cm_off(arow_lo, n, KD)) = v - hi;
+                *reinterpret_cast<float *>(As + cm_off(arow_hi, HQ, KD)) = hi;
+                *reinterpret_cast<float *>(As + cm_off(arow_lo, HQ, KD)) = v - hi;
             }
         }
         __syncthreads();
@@ -1011,16 +1021,18 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 __syncthreads();
             } else {
                 // rhs -> tf32 high parts and remainders in this column's two A rows,
-                // K = i - 1.  Iterations before the polish phase use the high parts only.
+                // K index HQ4*b + r: from the quarter's block, core-matrix slot r/4
+                // (128 bytes each), word r%4.  Rows that are not right-hand-side rows
+                // (x_0, padding) meet zero columns of B.  Iterations before the
+                // polish phase use the high parts only.
                 const bool split = l >= iters - polish;
+                float *ahi = reinterpret_cast<float *>(As + cm_off(arow_hi, tc_hq4(HQ) * b, KD));
+                float *alo = reinterpret_cast<float *>(As + cm_off(arow_lo, tc_hq4(HQ) * b, KD));
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
-                    const int i = i0 + r;
-                    if (i >= 1 && i < H) {
-                        const float hi = tf32_rna(rv[r]);
-                        *reinterpret_cast<float *>(As + cm_off(arow_hi, i - 1, KD)) = hi;
-                        if (split) *reinterpret_cast<float *>(As + cm_off(arow_lo, i - 1, KD)) = rv[r] - hi;
-                    }
+                    const float hi = tf32_rna(rv[r]);
+                    ahi[32 * (r >> 2) + (r & 3)] = hi;
+                    if (split) alo[32 * (r >> 2) + (r & 3)] = rv[r] - hi;
                 }
                 // A visible to the tensor core, the previous readback of D finished;
                 // a warp whose MMA wait ran out stops the block here
