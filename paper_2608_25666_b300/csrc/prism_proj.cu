@@ -74,6 +74,22 @@ prism_status fail(prism_status s, const char *fmt, ...)
 constexpr int CMAX = 64;         // columns per thread block
 constexpr int NTHREADS = 4 * CMAX;  // four threads per column (time quarters)
 
+// Solve-kernel variants: horizon chunks HQ (a horizon H runs on the first with
+// 4*HQ >= H).  Rows b*HQ + r with r < variant_rows_always_valid(HQ) exist in
+// every quarter b for every horizon that runs on the variant.
+__host__ __device__ constexpr int prev_variant_hq(int hq)
+{
+    return hq == 5 ? 3 : hq == 7 ? 5 : hq == 9 ? 7 : hq == 11 ? 9 : hq == 13 ? 11 : hq == 15 ? 13
+         : hq == 17 ? 15 : hq == 21 ? 17 : hq == 25 ? 21 : hq == 29 ? 25 : hq == 33 ? 29 : 0;
+}
+__host__ __device__ constexpr int variant_rows_always_valid(int hq)
+{
+    return (prev_variant_hq(hq) == 0 ? 2 : 4 * prev_variant_hq(hq) + 1) - 3 * hq > 0
+               ? ((prev_variant_hq(hq) == 0 ? 2 : 4 * prev_variant_hq(hq) + 1) - 3 * hq < hq
+                      ? (prev_variant_hq(hq) == 0 ? 2 : 4 * prev_variant_hq(hq) + 1) - 3 * hq : hq)
+               : 0;
+}
+
 // Bank-conflict-free column stride of the shared tiles: threads (c, b) of a warp
 // read row b*HQ + r, column c; rows of the four quarters must fall 8 banks apart.
 __host__ __device__ constexpr int col_stride(int hq) { return (hq & 1) ? 72 : 68; }
@@ -541,12 +557,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
     for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
 
-// Adds to out[k] (k < HQ) this quarter-thread's entries of tensor-memory
-// column col0 + 4k + t%4: a 16x128b load at column col0 + 4k gives thread t
-// lanes t/4 and t/4 + 8; both are added, or the first alone (!both).  Loads
-// are issued four at a time before one wait, and the registers pass through
-// the wait so no use is scheduled before it.
-template <int HQ>
+// Sets (ACC = false) or adds to (ACC = true) out[k] (k < HQ) this
+// quarter-thread's entries of tensor-memory column col0 + 4k + t%4: a 16x128b
+// load at column col0 + 4k gives thread t lanes t/4 and t/4 + 8; both are
+// summed, or the first alone (!both).  Loads are issued four at a time before
+// one wait, and the registers pass through the wait so no use is scheduled
+// before it.
+template <int HQ, bool ACC>
 __device__ __forceinline__ void tmem_add_quarter(uint32_t taddr, int col0, bool both, float out[HQ])
 {
 #pragma unroll
@@ -564,8 +581,10 @@ __device__ __forceinline__ void tmem_add_quarter(uint32_t taddr, int col0, bool 
                      :: "memory");
 #pragma unroll
         for (int g = 0; g < 4; ++g)
-            if (k0 + g < HQ)
-                out[k0 + g] += both ? __uint_as_float(a[g]) + __uint_as_float(c[g]) : __uint_as_float(a[g]);
+            if (k0 + g < HQ) {
+                const float v = both ? __uint_as_float(a[g]) + __uint_as_float(c[g]) : __uint_as_float(a[g]);
+                out[k0 + g] = ACC ? out[k0 + g] + v : v;
+            }
     }
 }
 
@@ -927,6 +946,18 @@ solve_kernel(const __grid_constant__ LaunchParams P)
             __syncthreads();
         }
 
+        // Acceleration / jerk row weights of local row r: rows below RSAFE exist
+        // in every quarter for every horizon of this variant, so only the first
+        // rows of quarter 0 differ from the uniform weight there; other rows
+        // (which may be padding) read the table.
+        constexpr int RSAFE = variant_rows_always_valid(HQ);
+        const auto accel_w = [&](int r) -> float {
+            return r < RSAFE ? ((r == 0 && b == 0) ? wa0 : wa) : was[i0 + r];
+        };
+        const auto jerk_w = [&](int r) -> float {
+            return r < RSAFE ? ((r == 0 && b == 0) ? 0.0f : ((r == 1 && b == 0) ? wj0 : wj)) : wjs[i0 + r];
+        };
+
         for (int l = 0; l < iters; ++l) {
             // ---- stencil phase: a3 slack / clip, a4 Fh^T, a6 multiplier -> rhs
             if (!TC && l > 0) load_xwin<HQ>(xs, CP, c, b, X);
@@ -958,10 +989,10 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     s.p[r] = wps[i] * t_p[r];
                     z = f0 ? clampf(2.0f * ya - t_a[r], cb.alo0, cb.ahi0) : clampf(2.0f * ya - t_a[r], cb.alo, cb.ahi);
                     t_a[r] = (z - ya) + t_a[r];
-                    s.a[r] = was[i] * t_a[r];
+                    s.a[r] = accel_w(r) * t_a[r];
                     z = f1 ? clampf(2.0f * yj - t_j[r], cb.jlo1, cb.jhi1) : clampf(2.0f * yj - t_j[r], cb.jlo, cb.jhi);
                     t_j[r] = (z - yj) + t_j[r];
-                    s.j[r] = wjs[i] * t_j[r];
+                    s.j[r] = jerk_w(r) * t_j[r];
                 }
                 apply_FT<HQ>(s, b, g);
 #pragma unroll
@@ -977,8 +1008,8 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                         const float yj = ya - (X.w[r + 1] - X.w[r]);
                         s.v[r] = wv * X.w[r + 2];
                         s.p[r] = wps[i] * cs;
-                        s.a[r] = was[i] * ya;
-                        s.j[r] = wjs[i] * yj;
+                        s.a[r] = accel_w(r) * ya;
+                        s.j[r] = jerk_w(r) * yj;
                     }
                     apply_FT<HQ>(s, b, g);
 #pragma unroll
@@ -999,8 +1030,8 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     const float pj = yj + (f1 ? clampf(yj, cb.jlo1, cb.jhi1) : clampf(yj, cb.jlo, cb.jhi));
                     s.v[r] = wv * pv;
                     s.p[r] = wps[i] * pp;
-                    s.a[r] = was[i] * pa;
-                    s.j[r] = wjs[i] * pj;
+                    s.a[r] = accel_w(r) * pa;
+                    s.j[r] = jerk_w(r) * pj;
                 }
                 apply_FT<HQ>(s, b, g);
 #pragma unroll
@@ -1084,10 +1115,8 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t tl = tbase + ((uint32_t)(32 * (warp & 3) + 16 * (warp >> 2)) << 16);
                     float xn[HQ];
-#pragma unroll
-                    for (int r = 0; r < HQ; ++r) xn[r] = 0.0f;
-                    tmem_add_quarter<HQ>(tl, 0, split, xn);
-                    if (split) tmem_add_quarter<HQ>(tl, ND, true, xn);
+                    tmem_add_quarter<HQ, false>(tl, 0, split, xn);
+                    if (split) tmem_add_quarter<HQ, true>(tl, ND, true, xn);
                     if (b == 0) xn[0] = colv ? v0j : 0.0f;   // x_0 = v0 exactly
                     if (last) {
                         float dm = 0.0f;
@@ -1440,6 +1469,15 @@ struct Variant {
      solve_kernel<HQv, PRISM_MODE_ADMM, true, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false>,       \
      solve_kernel<HQv, PRISM_MODE_ADMM, false, true>, solve_kernel<HQv, PRISM_MODE_PAPER, false, true>,       \
      solve_kernel<HQv, PRISM_MODE_ADMM, true, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, true>}
+// prev_variant_hq (used for the rows that always exist) must list the same chunks.
+constexpr int kVariantHQ[] = {3, 5, 7, 9, 11, 13, 15, 17, 21, 25, 29, 33};
+constexpr bool variant_chain_ok()
+{
+    for (int k = 0; k < (int)(sizeof(kVariantHQ) / sizeof(int)); ++k)
+        if (prev_variant_hq(kVariantHQ[k]) != (k ? kVariantHQ[k - 1] : 0)) return false;
+    return true;
+}
+static_assert(variant_chain_ok(), "prev_variant_hq does not match the variant list");
 const Variant kVariants[] = {VARIANT(3), VARIANT(5), VARIANT(7), VARIANT(9), VARIANT(11),
                              VARIANT(13), VARIANT(15), VARIANT(17), VARIANT(21), VARIANT(25),
                              VARIANT(29), VARIANT(33)};
