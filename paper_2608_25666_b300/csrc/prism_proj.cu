@@ -558,32 +558,44 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
 }
 
 // Sets (ACC = false) or adds to (ACC = true) out[k] (k < HQ) this
-// quarter-thread's entries of tensor-memory column col0 + 4k + t%4: a 16x128b
-// load at column col0 + 4k gives thread t lanes t/4 and t/4 + 8; both are
-// summed, or the first alone (!both).  Loads are issued four at a time before
-// one wait, and the registers pass through the wait so no use is scheduled
-// before it.
+// quarter-thread's entries of tensor-memory columns col0 + 4k + t%4, lanes t/4
+// and t/4 + 8 (summed; the first alone when !both).  One 16x128b.x4 load at
+// column col0 + 16g gives thread t, in register 2m + s, lane t/4 + 8s of column
+// col0 + 16g + 4m + t%4, i.e. time steps 4g .. 4g+3; up to four loads are
+// issued before one wait, and the registers pass through the wait so no use is
+// scheduled before it.  Columns past the HQ steps are read and ignored.
 template <int HQ, bool ACC>
 __device__ __forceinline__ void tmem_add_quarter(uint32_t taddr, int col0, bool both, float out[HQ])
 {
+    constexpr int NL = (HQ + 3) / 4;
 #pragma unroll
-    for (int k0 = 0; k0 < HQ; k0 += 4) {
-        uint32_t a[4], c[4];
+    for (int g0 = 0; g0 < NL; g0 += 4) {
+        uint32_t r[4][8];
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-            a[g] = c[g] = 0u;
-            if (k0 + g < HQ)
-                asm volatile("tcgen05.ld.sync.aligned.16x128b.x1.b32 {%0, %1}, [%2];"
-                             : "=r"(a[g]), "=r"(c[g]) : "r"(taddr + (uint32_t)(col0 + 4 * (k0 + g))));
+            if (g0 + g < NL) {
+                asm volatile("tcgen05.ld.sync.aligned.16x128b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                             : "=r"(r[g][0]), "=r"(r[g][1]), "=r"(r[g][2]), "=r"(r[g][3]), "=r"(r[g][4]),
+                               "=r"(r[g][5]), "=r"(r[g][6]), "=r"(r[g][7])
+                             : "r"(taddr + (uint32_t)(col0 + 16 * (g0 + g))));
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) r[g][e] = 0u;
+            }
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;"
-                     : "+r"(a[0]), "+r"(c[0]), "+r"(a[1]), "+r"(c[1]), "+r"(a[2]), "+r"(c[2]), "+r"(a[3]), "+r"(c[3])
+                     : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[0][4]), "+r"(r[0][5]), "+r"(r[0][6]), "+r"(r[0][7]), "+r"(r[1][0]), "+r"(r[1][1]), "+r"(r[1][2]), "+r"(r[1][3]), "+r"(r[1][4]), "+r"(r[1][5]), "+r"(r[1][6]), "+r"(r[1][7]), "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]), "+r"(r[2][4]), "+r"(r[2][5]), "+r"(r[2][6]), "+r"(r[2][7]), "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]), "+r"(r[3][4]), "+r"(r[3][5]), "+r"(r[3][6]), "+r"(r[3][7])
                      :: "memory");
 #pragma unroll
         for (int g = 0; g < 4; ++g)
-            if (k0 + g < HQ) {
-                const float v = both ? __uint_as_float(a[g]) + __uint_as_float(c[g]) : __uint_as_float(a[g]);
-                out[k0 + g] = ACC ? out[k0 + g] + v : v;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int k = 4 * (g0 + g) + m;
+                if (k < HQ) {
+                    const float v = both ? __uint_as_float(r[g][2 * m]) + __uint_as_float(r[g][2 * m + 1])
+                                         : __uint_as_float(r[g][2 * m]);
+                    out[k] = ACC ? out[k] + v : v;
+                }
             }
     }
 }
@@ -719,6 +731,8 @@ solve_kernel(const __grid_constant__ LaunchParams P)
     constexpr int HP = 4 * HQ;
     constexpr int CP = col_stride(HQ);
     constexpr int TMEM_COLS = tc_tmem_cols(HQ);
+    static_assert(!TC || tc_nrows(HQ) + 16 * ((HQ + 3) / 4) <= tc_tmem_cols(HQ),
+                  "the x4 readback reads past the tensor-memory allocation");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mma_bar;
