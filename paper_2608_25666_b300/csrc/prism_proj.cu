@@ -532,31 +532,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
     return done != 0;
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8])
-{
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[e]);
-}
-
-// 16 consecutive columns of this warp's lanes; columns past the allocation are
-// never requested (callers stay inside D).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
-{
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
-}
-
 // Sets (ACC = false) or adds to (ACC = true) out[k] (k < HQ) this
 // quarter-thread's entries of tensor-memory columns col0 + 4k + t%4, lanes t/4
 // and t/4 + 8 (summed; the first alone when !both).  One 16x128b.x4 load at
@@ -683,15 +658,15 @@ __device__ __forceinline__ void normals4(unsigned long long q, unsigned long lon
 // ===========================================================================
 // K3: persistent solve.  HQ = horizon steps per thread (H <= 4*HQ), MODE =
 // PRISM_MODE_ADMM / PRISM_MODE_PAPER, TC = K-apply on the tensor cores.
-// Shared memory: xs[(4HQ+2) x CP] floats (rows x_{-2}, x_{-1}, x_0 ..), rhs
-// [4HQ x CP], kb, wp, v0c, dres; the FP32-pipe variant adds Kt[n x MP]; the
-// tensor-core variant adds the operands A (128 x KD: the tile's right-hand
-// sides and, in column n, v0, as tf32 high parts and remainders in two rows per
-// column, 64 rows per column group) and B ([K' | kb'] high and low parts, ND x KD
-// each) and keeps one D (64 x ND fp32) per column group in tensor memory.  Two
-// MMAs per K-step (A Bhi, A Blo) give K' rhs + kb' v0 as the sum of the two rows
-// of a column, with the products of the two tf32 parts of both operands, i.e.
-// FP32-level accuracy.
+// Shared memory: xs[(4HQ+2) x CP] floats (rows x_{-2}, x_{-1}, x_0 ..), kb,
+// the position / acceleration / jerk weights, v0c, dres; the FP32-pipe variant
+// adds rhs [4HQ x CP] and Kt[n x MP]; the tensor-core variant adds the operands
+// A (128 x KD: per column the tf32 high parts of its right-hand side and, 8 rows
+// below, the remainders, plus v0 in one K slot) and B (2 ND x KD: [K' | kb']
+// high parts over low parts) and keeps D (128 x 2 ND fp32) in tensor memory.
+// One M = 128 MMA per K-step gives K' rhs + kb' v0 as the sum of a column's two
+// rows in both halves of D: the products of the two tf32 parts of both
+// operands, i.e. FP32-level accuracy.
 // ===========================================================================
 template <int HQ>
 __host__ __device__ constexpr int solve_min_blocks() { return HQ <= 17 ? 2 : 1; }
@@ -831,10 +806,11 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     const int i = xt - 1;                       // its row of [K' | kb']
                     constexpr int HQ4 = tc_hq4(HQ);
                     const int kb_ = kq / HQ4, kr = kq - kb_ * HQ4;
-                    const int xk = kb_ * HQ + kr;               // time step of K index kq
+                    const int rr = (kr & ~3) | ((kr & 3) ^ kb_);  // local row stored in this slot
+                    const int xk = kb_ * HQ + rr;               // time step of K index kq
                     const bool v0col = kq == HQ;
                     const int j = v0col ? n : xk - 1;           // its column of [K' | kb']
-                    const bool in = xt >= 1 && xt <= n && (v0col || (kr < HQ && xk >= 1 && xk <= n));
+                    const bool in = xt >= 1 && xt <= n && (v0col || (rr < HQ && xk >= 1 && xk <= n));
                     const int src = i * (n + 1) + j;
                     *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, kq, KD)) =
                         in ? (low ? p.Klo[src] : p.Khi[src]) : 0.0f;
@@ -900,7 +876,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
         if (b == 0) {
             xs[2 * CP + c] = colv ? v0j : 0.0f;
             if (TC) {
-                // column n of A: v0 of this column, split like the right-hand sides
+                // K slot HQ of A: v0 of this column, split like the right-hand sides
                 const float v = colv ? v0j : 0.0f;
                 const float hi = tf32_rna(v);
                 *reinterpret_cast<float *>(As + cm_off(arow_hi, HQ, KD)) = hi;
@@ -1066,18 +1042,22 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 __syncthreads();
             } else {
                 // rhs -> tf32 high parts and remainders in this column's two A rows,
-                // K index HQ4*b + r: from the quarter's block, core-matrix slot r/4
-                // (128 bytes each), word r%4.  Rows that are not right-hand-side rows
-                // (x_0, padding) meet zero columns of B.  Iterations before the
-                // polish phase use the high parts only.
+                // K index HQ4*b + 4(r/4) + (r%4 ^ b): from the quarter's block,
+                // core-matrix slot r/4 (128 bytes each), word r%4 ^ b (the XOR keeps
+                // the four quarter-threads of a column on different banks).  Rows
+                // that are not right-hand-side rows (x_0, padding) meet zero columns
+                // of B.  Iterations before the polish phase use the high parts only.
                 const bool split = l >= iters - polish;
                 float *ahi = reinterpret_cast<float *>(As + cm_off(arow_hi, tc_hq4(HQ) * b, KD));
-                float *alo = reinterpret_cast<float *>(As + cm_off(arow_lo, tc_hq4(HQ) * b, KD));
+                constexpr int LO = 8 * KD;   // floats from a column's high row to its low row
+                float *aw[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) aw[m] = ahi + (m ^ b);
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
                     const float hi = tf32_rna(rv[r]);
-                    ahi[32 * (r >> 2) + (r & 3)] = hi;
-                    if (split) alo[32 * (r >> 2) + (r & 3)] = rv[r] - hi;
+                    aw[r & 3][32 * (r >> 2)] = hi;
+                    if (split) aw[r & 3][32 * (r >> 2) + LO] = rv[r] - hi;
                 }
                 // A visible to the tensor core, the previous readback of D finished;
                 // a warp whose MMA wait ran out stops the block here
