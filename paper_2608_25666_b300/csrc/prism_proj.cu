@@ -390,20 +390,22 @@ __device__ __forceinline__ void xwin_from_regs(const float xq[HQ], int b, XWin<H
 template <int HQ>
 __device__ __forceinline__ void apply_FT(const Rows<HQ> &s, int b, float g[HQ])
 {
+    // Fh^T s = s_v + L^T s_p + D1^T (s_a + D1^T s_j), L^T a suffix sum and D1^T a
+    // first difference toward the future (zero past the horizon): with
+    // q = s_a + D1^T s_j the acceleration and jerk parts are one difference of q.
     float sps = 0.0f;
 #pragma unroll
     for (int r = 0; r < HQ; ++r) sps += s.p[r];
     float P = excl_suffix4(sps, b);
-    const float sa_n = from_next4(s.a[0], b);
-    const float sj_n0 = from_next4(s.j[0], b);
-    const float sj_n1 = from_next4(s.j[HQ > 1 ? 1 : 0], b);
+    const float sj_n = from_next4(s.j[0], b);
+    float q[HQ];
+#pragma unroll
+    for (int r = 0; r < HQ; ++r) q[r] = s.a[r] + (s.j[r] - ((r + 1 < HQ) ? s.j[(r + 1) % HQ] : sj_n));
+    const float q_n = from_next4(q[0], b);
 #pragma unroll
     for (int r = HQ - 1; r >= 0; --r) {
         P += s.p[r];
-        const float sa1 = (r + 1 < HQ) ? s.a[(r + 1) % HQ] : sa_n;
-        const float sj1 = (r + 1 < HQ) ? s.j[(r + 1) % HQ] : sj_n0;
-        const float sj2 = (r + 2 < HQ) ? s.j[(r + 2) % HQ] : ((r + 2 == HQ) ? sj_n0 : sj_n1);
-        g[r] = s.v[r] + P + (s.a[r] - sa1) + (s.j[r] - 2.0f * sj1 + sj2);
+        g[r] = (s.v[r] + P) + (q[r] - ((r + 1 < HQ) ? q[(r + 1) % HQ] : q_n));
     }
 }
 
