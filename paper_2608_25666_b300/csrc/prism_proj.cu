@@ -137,7 +137,7 @@ struct prism_proj_s {
     float *d_Kt32 = nullptr;             // [n][MP] transposed K, FP32, zero padded
     float *d_kb32 = nullptr;             // [MP]
     float *d_wp = nullptr;               // [PRISM_MAX_H] position-row weights
-    float *d_Khi = nullptr, *d_Klo = nullptr;   // [n][n+1] tf32 split of [K' | kb']
+    float *d_Khi = nullptr, *d_Klo = nullptr;   // [n+4][n+1] tf32 split of [K' | kb'] + quarter-prefix rows
     int *d_err = nullptr;                // tensor-core wait timeout flag
     double *d_wfull = nullptr;           // factor input: per-row weights (4 blocks x H)
     // plain comparator workspace
@@ -164,7 +164,7 @@ __device__ __forceinline__ double d2c(int m, int i)
 __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wrow,
                               double *__restrict__ K64, double *__restrict__ kb64,
                               float *__restrict__ Kt32, float *__restrict__ kb32, int MP,
-                              float *__restrict__ Khi32, float *__restrict__ Klo32)
+                              float *__restrict__ Khi32, float *__restrict__ Klo32, int hq)
 {
     extern __shared__ double Bs[];   // H*H
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -240,6 +240,22 @@ __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wr
         Khi32[e] = hi;
         Klo32[e] = (float)(kv - (double)hi);
     }
+    // Rows n + b (b = 0..3): the sum of x over the time steps before quarter b of
+    // the tensor-core kernel (quarters of hq steps), x_0 = v0 included, as the
+    // same linear map of [rhs | v0]: sum_{1 <= i < b*hq, i <= n} [K' | kb'][i-1]
+    // plus 1 on v0 when b >= 1.
+    for (int e = tid; e < 4 * (n + 1); e += nth) {
+        const int bq = e / (n + 1), j = e - bq * (n + 1);
+        const int iend = min(bq * hq - 1, n);
+        double acc = (j == n && bq >= 1) ? 1.0 : 0.0;
+        for (int i = 1; i <= iend; ++i) acc += (j < n) ? K64[(i - 1) * n + j] : kb64[i - 1];
+        uint32_t r;
+        const float kf = (float)acc;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(kf));
+        const float hi = __uint_as_float(r);
+        Khi32[(n + bq) * (n + 1) + j] = hi;
+        Klo32[(n + bq) * (n + 1) + j] = (float)(acc - (double)hi);
+    }
 }
 
 // ===========================================================================
@@ -257,8 +273,8 @@ struct SolveParams {
     const float *__restrict__ Kt;        // [n][MP]
     const float *__restrict__ kb;        // [MP]
     const float *__restrict__ wp;        // [>= H]
-    const float *__restrict__ Khi;       // [n][n+1] tf32 high part of [K' | kb'] (tensor-core path)
-    const float *__restrict__ Klo;       // [n][n+1] remainder [K' | kb'] - Khi
+    const float *__restrict__ Khi;       // [n+4][n+1] tf32 high part of [K' | kb'] and the quarter-prefix rows
+    const float *__restrict__ Klo;       // [n+4][n+1] remainder - Khi
     int *err;                            // set to 1 if a tensor-core wait ran out
     const float *x_init;                 // [N][H][J] warm-start iterate or NULL (x^0 = xi)
     const float *dual_init;              // [N][D][J] warm-start multiplier or NULL (0)
@@ -367,22 +383,19 @@ __device__ __forceinline__ void load_xwin(const float *__restrict__ xs, int CP, 
     X.pre = excl_prefix4(run, b);
 }
 
-// The x window from this quarter's time steps held in registers: the two halo
-// steps come from the previous quarter's thread (zero for quarter 0).
+// The x window from this quarter's time steps held in registers and the sum
+// of x over the earlier quarters (pre): the two halo steps come from the
+// previous quarter's thread (zero for quarter 0).
 template <int HQ>
-__device__ __forceinline__ void xwin_from_regs(const float xq[HQ], int b, XWin<HQ> &X)
+__device__ __forceinline__ void xwin_from_regs(const float xq[HQ], float pre, int b, XWin<HQ> &X)
 {
     const float h0 = __shfl_up_sync(0xffffffffu, xq[HQ - 2 >= 0 ? HQ - 2 : 0], 1, 4);
     const float h1 = __shfl_up_sync(0xffffffffu, xq[HQ - 1], 1, 4);
     X.w[0] = b > 0 ? h0 : 0.0f;
     X.w[1] = b > 0 ? h1 : 0.0f;
-    float run = 0.0f;
 #pragma unroll
-    for (int r = 0; r < HQ; ++r) {
-        X.w[r + 2] = xq[r];
-        run += xq[r];
-    }
-    X.pre = excl_prefix4(run, b);
+    for (int r = 0; r < HQ; ++r) X.w[r + 2] = xq[r];
+    X.pre = pre;
 }
 
 // g = Fh^T s for the quarter, given weighted row values s (zero on rows that
@@ -534,17 +547,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
     return done != 0;
 }
 
-// Sets (ACC = false) or adds to (ACC = true) out[k] (k < HQ) this
+// Sets (ACC = false) or adds to (ACC = true) out[k] (k < KN) this
 // quarter-thread's entries of tensor-memory columns col0 + 4k + t%4, lanes t/4
 // and t/4 + 8 (summed; the first alone when !both).  One 16x128b.x4 load at
 // column col0 + 16g gives thread t, in register 2m + s, lane t/4 + 8s of column
 // col0 + 16g + 4m + t%4, i.e. time steps 4g .. 4g+3; up to four loads are
 // issued before one wait, and the registers pass through the wait so no use is
 // scheduled before it.  Columns past the HQ steps are read and ignored.
-template <int HQ, bool ACC>
-__device__ __forceinline__ void tmem_add_quarter(uint32_t taddr, int col0, bool both, float out[HQ])
+template <int KN, bool ACC>
+__device__ __forceinline__ void tmem_add_quarter(uint32_t taddr, int col0, bool both, float out[KN])
 {
-    constexpr int NL = (HQ + 3) / 4;
+    constexpr int NL = (KN + 3) / 4;
 #pragma unroll
     for (int g0 = 0; g0 < NL; g0 += 4) {
         uint32_t r[4][8];
@@ -568,7 +581,7 @@ __device__ __forceinline__ void tmem_add_quarter(uint32_t taddr, int col0, bool 
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const int k = 4 * (g0 + g) + m;
-                if (k < HQ) {
+                if (k < KN) {
                     const float v = both ? __uint_as_float(r[g][2 * m]) + __uint_as_float(r[g][2 * m + 1])
                                          : __uint_as_float(r[g][2 * m]);
                     out[k] = ACC ? out[k] + v : v;
@@ -601,9 +614,10 @@ __global__ void diag_wait_kernel(uint32_t limit, int *flag)
 // first spare slot of quarter 0) carries v0, so D = K' rhs + kb' v0; entries of
 // B for time steps that are not right-hand-side rows (x_0, padding) are zero.
 // The outputs (N) are interleaved: D column 4k + b holds x_{b*HQ + k}, so one
-// 16x128b tensor-memory load hands each quarter-thread its own time steps,
-// padded to ND = 4*HQ + 4 rows of B (HQ is odd), so that the N-stacked operand
-// (2 ND rows) suits an M = 128 MMA (N in steps of 16).
+// 16x128b tensor-memory load hands each quarter-thread its own time steps; the
+// four columns 4*HQ + b hold the sum of x over the time steps before quarter b.
+// ND = 4*HQ + 4 rows of B (HQ is odd), so the N-stacked operand (2 ND rows)
+// suits an M = 128 MMA (N in steps of 16).
 __host__ __device__ constexpr int tc_hq4(int hq) { return round_up(hq, 4); }
 __host__ __device__ constexpr int tc_kd(int hq) { return 4 * tc_hq4(hq); }
 __host__ __device__ constexpr int tc_nrows(int hq) { return round_up(4 * hq, 8); }
@@ -708,7 +722,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
     constexpr int HP = 4 * HQ;
     constexpr int CP = col_stride(HQ);
     constexpr int TMEM_COLS = tc_tmem_cols(HQ);
-    static_assert(!TC || tc_nrows(HQ) + 16 * ((HQ + 3) / 4) <= tc_tmem_cols(HQ),
+    static_assert(!TC || tc_nrows(HQ) + 16 * ((HQ + 1 + 3) / 4) <= tc_tmem_cols(HQ),
                   "the x4 readback reads past the tensor-memory allocation");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t tmem_slot;
@@ -805,14 +819,15 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     const bool low = pr >= ND;
                     const int pc = low ? pr - ND : pr;
                     const int xt = (pc & 3) * HQ + (pc >> 2);   // time step of D column pc
-                    const int i = xt - 1;                       // its row of [K' | kb']
+                    const bool prefix = pc >= 4 * HQ;           // column 4HQ + b: quarter b's prefix sum
+                    const int i = prefix ? n + (pc & 3) : xt - 1;   // its row of [K' | kb'] / prefix rows
                     constexpr int HQ4 = tc_hq4(HQ);
                     const int kb_ = kq / HQ4, kr = kq - kb_ * HQ4;
                     const int rr = (kr & ~3) | ((kr & 3) ^ kb_);  // local row stored in this slot
                     const int xk = kb_ * HQ + rr;               // time step of K index kq
                     const bool v0col = kq == HQ;
                     const int j = v0col ? n : xk - 1;           // its column of [K' | kb']
-                    const bool in = xt >= 1 && xt <= n && (v0col || (rr < HQ && xk >= 1 && xk <= n));
+                    const bool in = (prefix || (xt >= 1 && xt <= n)) && (v0col || (rr < HQ && xk >= 1 && xk <= n));
                     const int src = i * (n + 1) + j;
                     *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, kq, KD)) =
                         in ? (low ? p.Klo[src] : p.Khi[src]) : 0.0f;
@@ -1110,9 +1125,9 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     // are not rewritten then)
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t tl = tbase + ((uint32_t)(32 * (warp & 3) + 16 * (warp >> 2)) << 16);
-                    float xn[HQ];
-                    tmem_add_quarter<HQ, false>(tl, 0, split, xn);
-                    if (split) tmem_add_quarter<HQ, true>(tl, ND, true, xn);
+                    float xn[HQ + 1];   // + the sum of x over the earlier quarters
+                    tmem_add_quarter<HQ + 1, false>(tl, 0, split, xn);
+                    if (split) tmem_add_quarter<HQ + 1, true>(tl, ND, true, xn);
                     if (b == 0) xn[0] = colv ? v0j : 0.0f;   // x_0 = v0 exactly
                     if (last) {
                         float dm = 0.0f;
@@ -1125,7 +1140,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                         dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, 2, 4));
                         if (b == 0) dres[c] = __float_as_uint(dm);
                     }
-                    xwin_from_regs<HQ>(xn, b, X);
+                    xwin_from_regs<HQ>(xn, xn[HQ], b, X);
                 }
             }
         }
@@ -1832,8 +1847,8 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
         CUDA_TRY(cudaMalloc(&h->d_kb32, sizeof(float) * std::max(MP, 4)));
         CUDA_TRY(cudaMalloc(&h->d_wp, sizeof(float) * PRISM_MAX_H));
         CUDA_TRY(cudaMalloc(&h->d_wfull, sizeof(double) * 4 * H));
-        CUDA_TRY(cudaMalloc(&h->d_Khi, sizeof(float) * std::max(n * (n + 1), 4)));
-        CUDA_TRY(cudaMalloc(&h->d_Klo, sizeof(float) * std::max(n * (n + 1), 4)));
+        CUDA_TRY(cudaMalloc(&h->d_Khi, sizeof(float) * (n + 4) * (n + 1)));
+        CUDA_TRY(cudaMalloc(&h->d_Klo, sizeof(float) * (n + 4) * (n + 1)));
         CUDA_TRY(cudaMalloc(&h->d_err, sizeof(int)));
         CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
     }
@@ -1853,8 +1868,10 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
     const size_t smem = sizeof(double) * H * H;
     CUDA_TRY(cudaFuncSetAttribute((const void *)factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const double rho_c = (mode == PRISM_MODE_PAPER ? 2.0 : 1.0) * rho;
+    const Variant *fv = pick_variant(H);
+    if (!fv) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", H);
     factor_kernel<<<1, 256, smem, s>>>(H, rho_c, h->d_wfull, h->d_K64, h->d_kb64, h->d_Kt32, h->d_kb32, MP,
-                                       h->d_Khi, h->d_Klo);
+                                       h->d_Khi, h->d_Klo, fv->hq);
     CUDA_TRY(cudaGetLastError());
     // the host tables above are stack memory: make sure the copies completed
     CUDA_TRY(cudaStreamSynchronize(s));
