@@ -103,6 +103,19 @@ def test_tc_horizon_limit():
     P.close()
 
 
+@pytest.mark.parametrize("H", [40, 60, 75, 90, 101, TC_MAX_H])
+def test_tc_every_large_variant(H):
+    """One horizon per tensor-core kernel variant not covered elsewhere (quarters
+    of 11, 15, 21, 25 and 29 steps; the last two at the shared-memory limit, one
+    block per SM), a ragged tile, both modes, against the oracle."""
+    for mode in (pp.MODE_ADMM, pp.MODE_PAPER):
+        b = workloads.make_custom(300 + H, 9, 7, H, 0.02, scale=0.8)
+        g = gpu_solve(b, 40, 1.0, mode=mode, prec=pp.PREC_TF32X3)
+        o = oracle_solve(b, 40, 1.0, mode=mode)
+        assert_parity(g, o, dual_tol=2e-4)
+        assert np.all(g["x"][:, 0, :] == b["v0"][None, :].astype(np.float64))
+
+
 @pytest.mark.parametrize("prec", [pp.PREC_FP32, pp.PREC_TF32X3], ids=["simt", "tc"])
 def test_realistic_full_size_sampled(prec):
     """N=4096, J=12, H=50, dt=0.02, 100 iterations, in the benchmark's launch
