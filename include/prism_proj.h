@@ -421,6 +421,17 @@ prism_status prism_proj_device_status(prism_proj_t h, void *cuda_stream);
  */
 prism_status prism_diag_wait_timeout(unsigned int poll_limit, int *timed_out);
 
+/*
+ * prism_test_fail_allocs -- host-side fault injection for tests (the paper has
+ * no counterpart).  After `skip` more device allocations made by this library,
+ * the next `count` of them fail as if the device were out of memory: the call
+ * that needed one returns PRISM_ERR_OOM, nothing is allocated for it and the
+ * handle or server stays usable (a later call allocates afresh).  (0, 0)
+ * switches it off.  Process-wide; not meant for use while other threads call
+ * the library.  No device is touched, so no GPU fault is involved.
+ */
+void prism_test_fail_allocs(int skip, int count);
+
 /* prism_proj_destroy -- free the handle and its device memory (synchronises the device). */
 prism_status prism_proj_destroy(prism_proj_t h);
 

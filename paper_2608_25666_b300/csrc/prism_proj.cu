@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -48,9 +49,38 @@
 #include <tuple>
 #include <vector>
 
+// Every device allocation of the library goes through dev_malloc, so a test can
+// make allocations fail on the host (prism_test_fail_allocs) without
+// exhausting the device: after g_alloc_skip more allocations, the next
+// g_alloc_fail ones report cudaErrorMemoryAllocation and allocate nothing.
+static std::atomic<int> g_alloc_skip{0}, g_alloc_fail{0};
+
+__attribute__((visibility("hidden"))) cudaError_t prism_internal_dev_malloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (g_alloc_fail.load() > 0) {
+        if (g_alloc_skip.load() > 0) {
+            --g_alloc_skip;
+        } else {
+            --g_alloc_fail;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 namespace {
 
 thread_local std::string g_last_error;
+
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    void *v = nullptr;
+    const cudaError_t e = prism_internal_dev_malloc(&v, bytes);
+    *p = static_cast<T *>(v);
+    return e;
+}
 
 prism_status fail(prism_status s, const char *fmt, ...)
 {
@@ -1811,7 +1841,7 @@ prism_status prism_proj_create(int J, int H, double dt, const double *q_min, con
     double hb[8 * PRISM_MAX_J];
     for (int b = 0; b < 8; ++b)
         for (int j = 0; j < J; ++j) hb[b * J + j] = arrs[b][j];
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_bounds, sizeof(double) * 8 * J);
+    if (e == cudaSuccess) e = dev_malloc(&h->d_bounds, sizeof(double) * 8 * J);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_bounds, hb, sizeof(double) * 8 * J, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         prism_status st = fail(e == cudaErrorMemoryAllocation ? PRISM_ERR_OOM : PRISM_ERR_CUDA, "create: %s",
@@ -1841,16 +1871,29 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int H = h->H, n = h->n, MP = h->MP;
     if (!h->d_K64) {
-        CUDA_TRY(cudaMalloc(&h->d_K64, sizeof(double) * n * n));
-        CUDA_TRY(cudaMalloc(&h->d_kb64, sizeof(double) * std::max(n, 1)));
-        CUDA_TRY(cudaMalloc(&h->d_Kt32, sizeof(float) * std::max(n * MP, 4)));
-        CUDA_TRY(cudaMalloc(&h->d_kb32, sizeof(float) * std::max(MP, 4)));
-        CUDA_TRY(cudaMalloc(&h->d_wp, sizeof(float) * PRISM_MAX_H));
-        CUDA_TRY(cudaMalloc(&h->d_wfull, sizeof(double) * 4 * H));
-        CUDA_TRY(cudaMalloc(&h->d_Khi, sizeof(float) * (n + 4) * (n + 1)));
-        CUDA_TRY(cudaMalloc(&h->d_Klo, sizeof(float) * (n + 4) * (n + 1)));
-        CUDA_TRY(cudaMalloc(&h->d_err, sizeof(int)));
-        CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+        // all or nothing: a failed allocation leaves the handle without a factor
+        // (and without half of its buffers), so a later call starts afresh
+        double *K64 = nullptr, *kb64 = nullptr, *wfull = nullptr;
+        float *Kt32 = nullptr, *kb32 = nullptr, *wp = nullptr, *Khi = nullptr, *Klo = nullptr;
+        int *err = nullptr;
+        cudaError_t e = dev_malloc(&K64, sizeof(double) * n * n);
+        if (e == cudaSuccess) e = dev_malloc(&kb64, sizeof(double) * std::max(n, 1));
+        if (e == cudaSuccess) e = dev_malloc(&Kt32, sizeof(float) * std::max(n * MP, 4));
+        if (e == cudaSuccess) e = dev_malloc(&kb32, sizeof(float) * std::max(MP, 4));
+        if (e == cudaSuccess) e = dev_malloc(&wp, sizeof(float) * PRISM_MAX_H);
+        if (e == cudaSuccess) e = dev_malloc(&wfull, sizeof(double) * 4 * H);
+        if (e == cudaSuccess) e = dev_malloc(&Khi, sizeof(float) * (n + 4) * (n + 1));
+        if (e == cudaSuccess) e = dev_malloc(&Klo, sizeof(float) * (n + 4) * (n + 1));
+        if (e == cudaSuccess) e = dev_malloc(&err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            cudaFree(K64); cudaFree(kb64); cudaFree(Kt32); cudaFree(kb32); cudaFree(wp);
+            cudaFree(wfull); cudaFree(Khi); cudaFree(Klo); cudaFree(err);
+            return fail(e == cudaErrorMemoryAllocation ? PRISM_ERR_OOM : PRISM_ERR_CUDA, "factor buffers: %s",
+                        cudaGetErrorString(e));
+        }
+        h->d_K64 = K64; h->d_kb64 = kb64; h->d_Kt32 = Kt32; h->d_kb32 = kb32; h->d_wp = wp;
+        h->d_wfull = wfull; h->d_Khi = Khi; h->d_Klo = Klo; h->d_err = err;
     }
     const Weights w = make_weights(scale, h->dt);
     double wfull[4 * PRISM_MAX_H];
@@ -1983,7 +2026,9 @@ prism_status prism_proj_solve_plain(prism_proj_t h, int batch, const float *q0, 
             h->d_work = nullptr;
             h->work_elems = 0;
         }
-        CUDA_TRY(cudaMalloc(&h->d_work, need * sizeof(float)));
+        float *wk = nullptr;
+        CUDA_TRY(dev_malloc(&wk, need * sizeof(float)));
+        h->d_work = wk;
         h->work_elems = need;
     }
     const int tpb = 128;
@@ -2044,7 +2089,9 @@ prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_ho
             h->d_stage = nullptr;
             h->stage_elems = 0;
         }
-        CUDA_TRY(cudaMalloc(&h->d_stage, need * sizeof(float)));
+        float *sg = nullptr;
+        CUDA_TRY(dev_malloc(&sg, need * sizeof(float)));
+        h->d_stage = sg;
         h->stage_elems = need;
     }
     float *d_x = h->d_stage;                 // samples in, trajectories out (in place)
@@ -2083,7 +2130,7 @@ prism_status prism_diag_wait_timeout(unsigned int poll_limit, int *timed_out)
     if (poll_limit < 1 || poll_limit > (1u << 22)) return fail(PRISM_ERR_INVALID_ARG, "poll_limit outside [1, 2^22]");
     *timed_out = -1;
     int *d_flag = nullptr;
-    CUDA_TRY(cudaMalloc(&d_flag, sizeof(int)));
+    CUDA_TRY(dev_malloc(&d_flag, sizeof(int)));
     cudaError_t e = cudaMemset(d_flag, 0xff, sizeof(int));
     if (e == cudaSuccess) {
         diag_wait_kernel<<<1, 32>>>(poll_limit, d_flag);
@@ -2252,11 +2299,15 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             st = variant_config(Hmax, g.mode, g.tc, true, n_max, MP_max, dev, g.fn, g.smem, g.bps, hq);
             if (st) break;
             if (!g.params.empty()) {
-                cudaError_t e = cudaMalloc(&g.d_params, sizeof(SolveParams) * g.params.size());
+                cudaError_t e = dev_malloc(&g.d_params, sizeof(SolveParams) * g.params.size());
                 if (e == cudaSuccess)
                     e = cudaMemcpy(g.d_params, g.params.data(), sizeof(SolveParams) * g.params.size(),
                                    cudaMemcpyHostToDevice);
-                if (e != cudaSuccess) { st = fail(PRISM_ERR_CUDA, "plan descriptors: %s", cudaGetErrorString(e)); break; }
+                if (e != cudaSuccess) {
+                    st = fail(e == cudaErrorMemoryAllocation ? PRISM_ERR_OOM : PRISM_ERR_CUDA, "plan descriptors: %s",
+                              cudaGetErrorString(e));
+                    break;
+                }
             }
             g.lp.many = g.d_params;
             cudaError_t e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
@@ -2403,6 +2454,12 @@ prism_status prism_proj_destroy(prism_proj_t h)
     cudaFree(h->d_stage);
     delete h;
     return PRISM_OK;
+}
+
+void prism_test_fail_allocs(int skip, int count)
+{
+    g_alloc_skip = skip > 0 ? skip : 0;
+    g_alloc_fail = count > 0 ? count : 0;
 }
 
 }  // extern "C"

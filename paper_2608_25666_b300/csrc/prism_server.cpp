@@ -40,8 +40,10 @@
 #include <unordered_map>
 #include <vector>
 
-// Records the thread-local error text of libprism_proj (defined in prism_proj.cu).
+// Records the thread-local error text of libprism_proj; device allocations of the
+// library (both defined in prism_proj.cu).
 prism_status prism_internal_fail(prism_status s, const char *msg);
+cudaError_t prism_internal_dev_malloc(void **p, size_t bytes);
 
 struct Server;
 
@@ -326,7 +328,7 @@ prism_status prism_server_create(size_t mem_budget_bytes, int max_inflight, doub
     S.deadline_ms = deadline_ms;
     cudaError_t e = cudaGetDevice(&S.device);
     char *base = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&base, mem_budget_bytes);
+    if (e == cudaSuccess) e = prism_internal_dev_malloc(reinterpret_cast<void **>(&base), mem_budget_bytes);
     if (e != cudaSuccess) {
         delete ps;
         return sfail(e == cudaErrorMemoryAllocation ? PRISM_ERR_OOM : PRISM_ERR_CUDA, "server arena: %s",

@@ -84,6 +84,8 @@ def lib() -> ctypes.CDLL:
             L.prism_proj_device_status.argtypes = [P, P]
             L.prism_diag_wait_timeout.argtypes = [ctypes.c_uint, ctypes.POINTER(i)]
             L.prism_diag_wait_timeout.restype = i
+            L.prism_test_fail_allocs.argtypes = [i, i]
+            L.prism_test_fail_allocs.restype = None
             for name in ("create", "factor", "solve", "solve_ex", "solve_plain", "solve_host",
                          "check_fp64", "shift_state", "get_factor", "query", "device_status", "destroy"):
                 getattr(L, "prism_proj_" + name).restype = i
@@ -465,6 +467,12 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def test_fail_allocs(skip: int, count: int) -> None:
+    """prism_test_fail_allocs: after ``skip`` device allocations of the library, fail
+    the next ``count`` as out-of-memory (host-side fault injection; (0, 0) = off)."""
+    lib().prism_test_fail_allocs(int(skip), int(count))
 
 
 def diag_wait_timeout(poll_limit: int = 1000) -> bool:

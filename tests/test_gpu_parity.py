@@ -225,6 +225,62 @@ def test_bounded_wait_times_out_and_the_context_survives():
     assert e.value.status == 1
 
 
+def test_allocation_failures_leave_handles_usable():
+    """Host-injected out-of-memory at every device allocation of create, factor,
+    the plain comparator's workspace, the host-buffer staging and the serving
+    arena: each call fails with PRISM_ERR_OOM, and the next call succeeds and
+    still matches the oracle (no half-built factor is kept)."""
+    import torch
+    b = workloads.make_custom(71, 5, 4, 25, 0.05)
+    xi, q0, v0 = to_dev(b)
+    try:
+        pp.test_fail_allocs(0, 1)
+        with pytest.raises(pp.PrismError) as e:
+            pp.Projector(4, 25, 0.05, b["bounds"])
+        assert e.value.status == 5
+        pp.test_fail_allocs(0, 0)
+        P = pp.Projector(4, 25, 0.05, b["bounds"])
+        for k in range(9):                      # factor allocates nine buffers
+            pp.test_fail_allocs(k, 1)
+            with pytest.raises(pp.PrismError) as e:
+                P.factor(1.0, prec=pp.PREC_TF32X3)
+            assert e.value.status == 5, k
+        pp.test_fail_allocs(0, 0)
+        P.factor(1.0, prec=pp.PREC_TF32X3)
+        x, pr, du = P.solve(q0, v0, xi, 30)
+        torch.cuda.synchronize()
+        g = {"x": x.cpu().numpy().astype(np.float64), "primal": pr.cpu().numpy().astype(np.float64),
+             "dual": du.cpu().numpy().astype(np.float64)}
+        assert_parity(g, oracle_solve(b, 30, 1.0), dual_tol=2e-4)
+        pp.test_fail_allocs(0, 1)
+        with pytest.raises(pp.PrismError) as e:
+            P.solve_plain(q0, v0, xi, 30)
+        assert e.value.status == 5
+        pp.test_fail_allocs(0, 0)
+        xp, _, _ = P.solve_plain(q0, v0, xi, 30)
+        torch.cuda.synchronize()
+        assert float((xp - x).abs().max()) <= X_TOL
+        hx = torch.from_numpy(b["xi"]).contiguous()
+        hq0, hv0 = torch.from_numpy(b["q0"]).contiguous(), torch.from_numpy(b["v0"]).contiguous()
+        hout = torch.empty_like(hx)
+        pp.test_fail_allocs(0, 1)
+        with pytest.raises(pp.PrismError) as e:
+            P.solve_host(hq0, hv0, hx, 30, out=hout)
+        assert e.value.status == 5
+        pp.test_fail_allocs(0, 0)
+        P.solve_host(hq0, hv0, hx, 30, out=hout)
+        assert float((hout - x.cpu()).abs().max()) <= 1e-6
+        P.close()
+        pp.test_fail_allocs(0, 1)
+        with pytest.raises(pp.PrismError) as e:
+            pp.Server(mem_budget_bytes=1 << 24, max_inflight=1)
+        assert e.value.status == 5
+        pp.test_fail_allocs(0, 0)
+        pp.Server(mem_budget_bytes=1 << 24, max_inflight=1).close()
+    finally:
+        pp.test_fail_allocs(0, 0)
+
+
 def test_unscaled_rows_fp32_error_is_reported():
     """Printed (unscaled) rows: the FP32 iteration is ill-conditioned; the
     error against the oracle is measured, not gated at 1e-4."""
