@@ -5,8 +5,10 @@
 //   factor_kernel      one-time per-shape factorisation in FP64 (Sec. III-D
 //                      "Pre-computable factorization", KKT matrix of Eq. admm_primal)
 //   solve_kernel<HQ,M> the persistent solve: one thread block owns a tile of
-//                      columns (samples x joints) for all iterations, with the
-//                      iterate in shared memory and the multiplier in registers
+//                      columns (samples x joints) for all iterations, the
+//                      multiplier in registers; the K-apply on the tensor cores
+//                      (iterate in registers, D in tensor memory) or on the
+//                      FP32 pipe (iterate in shared memory)
 //   plain_kernel       the plain FP32 comparator: one thread per column, state in
 //                      a device workspace, no tiling
 //   check_kernel       FP64 feasibility check of returned trajectories
