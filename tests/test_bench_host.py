@@ -1,0 +1,36 @@
+"""Host-side helpers of bench.py (no GPU): the algorithmic work count used by
+the roofline, the whole-job throughput, and the code hash that keys recorded
+DRAM traffic to the kernel source it was measured on."""
+import importlib.util
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_flops_per_column_iteration_matches_the_stated_count():
+    b = _bench()
+    # 2(H-1)^2 + 43H - 19 flops per column and iteration (6 933 at H = 50)
+    assert b.flops_per_column_iteration(50) == 6933
+    for H in (2, 13, 64, 132):
+        assert b.flops_per_column_iteration(H) == 2 * (H - 1) ** 2 + 43 * H - 19
+
+
+def test_whole_job_throughput_counts_every_rank():
+    b = _bench()
+    assert b.weak_scaling_value(1, 4096, 10, 10.0) == 4096 * 10 / 0.010
+    assert b.weak_scaling_value(4, 4096, 10, 10.0) == 4 * 4096 * 10 / 0.010
+
+
+def test_code_hash_ignores_comments_and_layout_only():
+    b = _bench()
+    src = "int f(int a) {\n  return a + 1;  // add one\n}\n/* note */\n"
+    assert b.code_hash(src) == b.code_hash("int f(int a) { return a + 1; }")
+    assert b.code_hash(src) != b.code_hash("int f(int a) { return a + 2; }")
+    assert len(b.kernel_source_hash()) == 16
