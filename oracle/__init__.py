@@ -10,6 +10,7 @@ paper (Sec. III-D) it follows.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -38,30 +39,51 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _bind(path: str):
+    """Open a compiled oracle library and declare its entry points."""
+    lib = ctypes.CDLL(path)
+    d, i, ll = ctypes.c_double, ctypes.c_int, ctypes.c_longlong
+    P = ctypes.c_void_p
+    lib.oracle_build_G_h.argtypes = [i, d, P, d, d, P, P]
+    lib.oracle_build_G_h.restype = i
+    lib.oracle_kkt_inverse.argtypes = [i, i, i, d, d, P, P]
+    lib.oracle_kkt_inverse.restype = i
+    lib.oracle_solve_batch.argtypes = [i, i, i, i, i, d, P, P, P, P, i, d, P, P, P, P, P,
+                                       P, P, ll, i]
+    lib.oracle_solve_batch.restype = i
+    lib.oracle_exact_projection.argtypes = [i, d, P, d, d, P, d, d, ll, P, P]
+    lib.oracle_exact_projection.restype = ll
+    lib.oracle_philox4x32_10.argtypes = [P, P, P]
+    lib.oracle_philox4x32_10.restype = None
+    lib.oracle_sample_batch.argtypes = [i, i, i, P, P, ctypes.c_ulonglong, ctypes.c_ulonglong, P]
+    lib.oracle_sample_batch.restype = i
+    lib.oracle_num_threads.argtypes = []
+    lib.oracle_num_threads.restype = i
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            d, i, ll = ctypes.c_double, ctypes.c_int, ctypes.c_longlong
-            P = ctypes.c_void_p
-            lib.oracle_build_G_h.argtypes = [i, d, P, d, d, P, P]
-            lib.oracle_build_G_h.restype = i
-            lib.oracle_kkt_inverse.argtypes = [i, i, i, d, d, P, P]
-            lib.oracle_kkt_inverse.restype = i
-            lib.oracle_solve_batch.argtypes = [i, i, i, i, i, d, P, P, P, P, i, d, P, P, P, P, P,
-                                               P, P, ll, i]
-            lib.oracle_solve_batch.restype = i
-            lib.oracle_exact_projection.argtypes = [i, d, P, d, d, P, d, d, ll, P, P]
-            lib.oracle_exact_projection.restype = ll
-            lib.oracle_philox4x32_10.argtypes = [P, P, P]
-            lib.oracle_philox4x32_10.restype = None
-            lib.oracle_sample_batch.argtypes = [i, i, i, P, P, ctypes.c_ulonglong, ctypes.c_ulonglong, P]
-            lib.oracle_sample_batch.restype = i
-            lib.oracle_num_threads.argtypes = []
-            lib.oracle_num_threads.restype = i
-            _lib = lib
+            _lib = _bind(build())
     return _lib
+
+
+@contextlib.contextmanager
+def swapped_library(path: str):
+    """Run the oracle's functions on another build of prism_oracle.c (a copy
+    with a planted mistake, compiled by a test) inside the ``with`` block."""
+    global _lib
+    old = _load()
+    new = _bind(path)
+    with _lock:
+        _lib = new
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = old
 
 
 def _p(a):

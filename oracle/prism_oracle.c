@@ -40,7 +40,11 @@
  * against brute-force active-set enumeration (H<=5), the H=2 closed form, KKT
  * certificates, idempotence, non-expansiveness and row-scaling invariance; the
  * first primal step of both modes against its argmin definition (least
- * squares); the PAPER fixed point against its stationarity relation.
+ * squares); every ADMM iteration against the dual feasibility of scaled ADMM
+ * (x - xi + rho F'^T u in span(e1)) and its slack against the box projection
+ * (normal-cone condition); the residuals against their definitions; the
+ * PAPER fixed point against its stationarity relation.  Planted mistakes in
+ * a copy of this file each fail a pin (tests/test_oracle_mutations.py).
  * PARITY UNPINNED: the factor delta/2 of the PAPER-mode multiplier step
  * (Eq. admm_dual).  No fact outside the printed formula fixes it (the fixed
  * point is the same for any positive factor), so a change of that factor

@@ -368,3 +368,108 @@ def test_paper_iteration_is_not_the_projection():
             assert d_paper >= d_pi - 1e-9
             gaps.append(d_paper - d_pi)
     assert max(gaps) > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# Per-iteration pins of the ADMM reading.  The tests above fix the first primal
+# step and the limit; these fix every iteration, so that a changed multiplier
+# step or a changed slack step (which have the same limit) is caught after the
+# same finite number of iterations that the GPU parity tests compare.
+# ---------------------------------------------------------------------------
+ADMM_CASES = [(6, 0.05, 1.0, oracle.SCALE_ROWNORM), (12, 0.02, 0.4, oracle.SCALE_ROWNORM),
+              (20, 0.1, 2.5, oracle.SCALE_NONE), (30, 0.05, 1.0, oracle.SCALE_ROWNORM)]
+
+
+def _admm_state(xi, bnd, q0, v0, H, dt, L, rho, scale, x_init=None, dual_init=None):
+    r = oracle.solve_batch(xi.reshape(1, H, 1), [q0], [v0], bnd.reshape(8, 1), dt, L, rho,
+                           scale=scale, want_dual_state=True,
+                           x_init=None if x_init is None else x_init.reshape(1, H, 1),
+                           dual_init=None if dual_init is None else dual_init.reshape(1, -1, 1))
+    return r["x"][0, :, 0], r["dual_state"][0, :, 0], r
+
+
+@pytest.mark.parametrize("H,dt,rho,scale", ADMM_CASES)
+def test_admm_dual_feasibility_after_every_iteration(H, dt, rho, scale):
+    """Scaled ADMM (Boyd et al. 2011, Sec. 3.3): with the multiplier step
+    u <- u + F'x - z, the x-step's optimality condition becomes dual
+    feasibility of the new pair, x^l - xi + rho F'^T u^l in span(e1) (the
+    x_1 = v0 multiplier), after EVERY iteration l.  Any other step size breaks
+    it.  F' is built here from the printed G (pinned above) with unit rows."""
+    rng = np.random.default_rng(60 + H)
+    xi, bnd, q0, v0 = rand_case(rng, H, dt, tight=0.5)
+    Fs, _, _, _, _ = _scaled_plus_rows(H, dt, bnd, q0, v0, rownorm=(scale == oracle.SCALE_ROWNORM))
+    # rounding bound of one x-step: a few ulps times the condition number of
+    # I + rho F'^T F' times the size of the terms (1e-15 with unit rows; the
+    # printed rows carry 1/dt^2 and a condition number near 1e6)
+    kappa = np.linalg.cond(np.eye(H) + rho * Fs.T @ Fs)
+    eps = 16 * np.finfo(float).eps * kappa
+
+    def tol(u):
+        return eps * max(1.0, float(np.max(np.abs(rho * Fs.T @ u))), float(np.max(np.abs(xi))))
+
+    seen_active = False
+    for L in range(1, 11):
+        x, u, _ = _admm_state(xi, bnd, q0, v0, H, dt, L, rho, scale)
+        g = x - xi + rho * Fs.T @ u
+        assert np.max(np.abs(g[1:])) <= tol(u), (L, np.max(np.abs(g[1:])), tol(u))
+        seen_active |= bool(np.max(np.abs(u)) > 1e-3)
+    assert seen_active   # the case exercises active constraints
+    assert eps < 1e-6    # far below the 1e-2 .. 1 that a wrong step leaves
+    # the same holds from a warm start (given iterate and multiplier)
+    x5, u5, _ = _admm_state(xi, bnd, q0, v0, H, dt, 5, rho, scale)
+    xw, uw, _ = _admm_state(xi, bnd, q0, v0, H, dt, 3, rho, scale, x_init=x5, dual_init=u5)
+    g = xw - xi + rho * Fs.T @ uw
+    assert np.max(np.abs(g[1:])) <= tol(uw)
+
+
+@pytest.mark.parametrize("H,dt,rho,scale", ADMM_CASES)
+def test_admm_slack_step_is_the_box_projection(H, dt, rho, scale):
+    """The slack of iteration l is z^l = u^{l-1} + F'x^l - u^l (the multiplier
+    step read backwards).  It must be the Euclidean projection of
+    w = F'x^{l-1} + u^{l-1} onto the box [lo', hi']: z inside the box and
+    w - z in the box's normal cone at z (positive only where z sits on hi',
+    negative only where it sits on lo').  This fixes which iterate and which
+    multiplier the slack step sees and that it clips before the x-step."""
+    rng = np.random.default_rng(70 + H)
+    xi, bnd, q0, v0 = rand_case(rng, H, dt, tight=0.5)
+    Fs, hi, lo, _, _ = _scaled_plus_rows(H, dt, bnd, q0, v0, rownorm=(scale == oracle.SCALE_ROWNORM))
+    x0 = xi.copy()
+    x0[0] = v0
+    u_prev, x_prev = np.zeros(4 * H - 1), x0
+    n_active = 0
+    for L in range(1, 9):
+        x, u, _ = _admm_state(xi, bnd, q0, v0, H, dt, L, rho, scale)
+        z = u_prev + Fs @ x - u
+        w = Fs @ x_prev + u_prev
+        scl = 1e-11 * max(1.0, float(np.max(np.abs(w))))
+        assert np.all(z >= lo - scl) and np.all(z <= hi + scl), L
+        r = w - z
+        on_hi = np.abs(z - hi) <= scl
+        on_lo = np.abs(z - lo) <= scl
+        assert np.all((r <= scl) | on_hi), L
+        assert np.all((r >= -scl) | on_lo), L
+        n_active += int(np.sum(np.abs(r) > 1e-6))
+        u_prev, x_prev = u, x
+    assert n_active > 0
+
+
+def test_admm_residuals_are_their_definitions():
+    """primal = max(|x_1 - v0|, row-normalised violation of the derivative
+    bounds), the rows and their norms taken from the derivative map itself;
+    dual = max |x^L - x^{L-1}| from two runs of L-1 and L iterations."""
+    rng = np.random.default_rng(81)
+    H, dt, rho = 14, 0.05, 1.3
+    xi, bnd, q0, v0 = rand_case(rng, H, dt, tight=0.6)
+    A, c0 = affine_rows(H, dt, q0, v0)
+    lo, hi = bounds_vec(bnd, H)
+    nrm = np.linalg.norm(A, axis=1)
+    for L in (0, 1, 4, 9):
+        x, _, r = _admm_state(xi, bnd, q0, v0, H, dt, L, rho, oracle.SCALE_ROWNORM)
+        c = A @ x + c0
+        ref = max(abs(x[0] - v0), float(np.max(np.maximum(0.0, np.maximum(c - hi, lo - c)) / nrm)))
+        assert r["primal"][0, 0] == pytest.approx(ref, rel=1e-12, abs=1e-14)
+        if L == 0:
+            assert r["dual"][0, 0] == 0.0
+        else:
+            xp, _, _ = _admm_state(xi, bnd, q0, v0, H, dt, L - 1, rho, oracle.SCALE_ROWNORM)
+            assert r["dual"][0, 0] == pytest.approx(float(np.max(np.abs(x - xp))), rel=1e-12, abs=1e-15)
