@@ -360,7 +360,12 @@ prism_status prism_proj_describe(prism_proj_t h, int dims[6], double *rho);
  * prism_server_wait: wait up to timeout_ms (< 0: forever) for a ticket;
  *   *state = 0 queued, 1 running, 2 done, 3 dropped, 4 failed; *latency_ms =
  *   submit-to-completion time (done) or -1.  A finished ticket is forgotten
- *   after it has been waited for.
+ *   after it has been waited for.  A failed request returns PRISM_ERR_CUDA
+ *   (an enqueue failed) or PRISM_ERR_TIMEOUT (a bounded device-side wait of
+ *   its solve ran out, see prism_proj_device_status: its outputs are invalid).
+ *   Each request reads and clears its handle's timeout flag on its own stream
+ *   after the solve, without a host synchronisation; after a failed request
+ *   the controller's next request starts cold (no warm-start multiplier).
  * prism_server_stats: out[0] completed, out[1] dropped, out[2] failed, out[3]
  *   p50 and out[4] p99 latency (ms), out[5] max latency, out[6] deadline misses
  *   (late or dropped), out[7] completed trajectories, out[8] trajectories/s
@@ -431,6 +436,16 @@ prism_status prism_diag_wait_timeout(unsigned int poll_limit, int *timed_out);
  * the library.  No device is touched, so no GPU fault is involved.
  */
 void prism_test_fail_allocs(int skip, int count);
+
+/*
+ * prism_test_set_device_flag -- host-side fault injection for tests (the paper
+ * has no counterpart): writes `value` (synchronously, cudaMemset) into the
+ * handle's device-side timeout flag, exactly what a solve whose bounded wait
+ * ran out leaves behind, so that the reporting paths (device_status,
+ * solve_host, the serving loop, plans) can be tested without any device-side
+ * fault.  The handle must be factored.
+ */
+prism_status prism_test_set_device_flag(prism_proj_t h, int value);
 
 /* prism_proj_destroy -- free the handle and its device memory (synchronises the device). */
 prism_status prism_proj_destroy(prism_proj_t h);

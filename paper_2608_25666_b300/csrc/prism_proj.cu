@@ -1279,6 +1279,9 @@ solve_kernel(const __grid_constant__ LaunchParams P)
         }
     }
     if (TC) {
+        // after a timeout the MMAs of the last commit may still be running: one
+        // more bounded wait for that phase before the tensor memory is freed
+        if (aborted && tid == 0) (void)mbar_wait(smem_addr(&mma_bar), mma_phase ^ 1u);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (warp == 0)
@@ -2365,9 +2368,20 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             g.tuned_ms = ms;
         }
         if (!st) {
-            int err = 0;
-            cudaMemcpy(&err, probs[0].h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-            if (err) st = fail(PRISM_ERR_CUDA, "tensor-core wait timed out during autotuning");
+            // every launch wrote its timeouts into its own problem's handle: read
+            // and clear the flag of each distinct handle
+            CUDA_TRY(cudaDeviceSynchronize());
+            std::vector<prism_proj_t> seen;
+            for (int k = 0; k < nprob && !st; ++k) {
+                prism_proj_t hk = probs[k].h;
+                if (std::find(seen.begin(), seen.end(), hk) != seen.end()) continue;
+                seen.push_back(hk);
+                int err = 0;
+                cudaError_t e = cudaMemcpy(&err, hk->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess && err) e = cudaMemset(hk->d_err, 0, sizeof(int));
+                if (e != cudaSuccess) st = fail(PRISM_ERR_CUDA, "autotune flags: %s", cudaGetErrorString(e));
+                else if (err) st = fail(PRISM_ERR_TIMEOUT, "problem %d: a device-side wait ran out during autotuning", k);
+            }
         }
     }
     if (!st) plan_size_grids(pl);
@@ -2464,10 +2478,25 @@ void prism_test_fail_allocs(int skip, int count)
     g_alloc_fail = count > 0 ? count : 0;
 }
 
+prism_status prism_test_set_device_flag(prism_proj_t h, int value)
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    if (!h->d_err) return fail(PRISM_ERR_NOT_FACTORED, "prism_proj_factor has not been called");
+    const int v = value ? 1 : 0;
+    CUDA_TRY(cudaMemcpy(h->d_err, &v, sizeof(int), cudaMemcpyHostToDevice));
+    return PRISM_OK;
+}
+
 }  // extern "C"
 
 // Shared with the serving loop (prism_server.cpp); not part of the C ABI.
 __attribute__((visibility("hidden"))) prism_status prism_internal_fail(prism_status s, const char *msg)
 {
     return fail(s, "%s", msg);
+}
+
+__attribute__((visibility("hidden"))) int *prism_internal_err_flag(prism_proj_t h)
+{
+    return h ? h->d_err : nullptr;
 }

@@ -41,9 +41,11 @@
 #include <vector>
 
 // Records the thread-local error text of libprism_proj; device allocations of the
-// library (both defined in prism_proj.cu).
+// library; the device word in which a handle's solves report a wait that ran
+// out (all defined in prism_proj.cu).
 prism_status prism_internal_fail(prism_status s, const char *msg);
 cudaError_t prism_internal_dev_malloc(void **p, size_t bytes);
+int *prism_internal_err_flag(prism_proj_t h);
 
 struct Server;
 
@@ -75,6 +77,7 @@ struct Request {
     double t_submit = 0.0, t_done = 0.0;
     std::atomic<int> state{Q_QUEUED};
     bool retired = false;          // buffers released and statistics recorded
+    prism_status fail_status = PRISM_OK;   // why a failed request failed
     size_t off = 0, bytes = 0;     // arena block of its staging buffers
     int slot = -1;
     struct Server *srv = nullptr;
@@ -155,6 +158,7 @@ struct Server {
     std::vector<Controller> ctrls;
     std::vector<cudaStream_t> streams;
     std::vector<std::shared_ptr<Request>> slot_req;
+    int *slot_flag = nullptr;          // pinned host words: each slot's copy of its solve's timeout flag
     std::deque<std::shared_ptr<Request>> fifo;
     std::unordered_map<unsigned long long, std::shared_ptr<Request>> tickets;
     unsigned long long next_ticket = 1;
@@ -214,6 +218,13 @@ bool Server::enqueue(const std::shared_ptr<Request> &r, const Controller &c, boo
     if (ok)
         ok = prism_proj_solve_ex(c.h, c.N, d_q0, d_v0, d_xi, c.iters, c.rho, &o, d_out, d_pr, nullptr, s) ==
              PRISM_OK;
+    // the handle's timeout flag after this solve, read at retire without a host
+    // sync, then cleared for the next launch of the handle
+    int *d_flag = prism_internal_err_flag(c.h);
+    slot_flag[r->slot] = 0;
+    if (ok && d_flag)
+        ok = cudaMemcpyAsync(&slot_flag[r->slot], d_flag, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+             cudaMemsetAsync(d_flag, 0, sizeof(int), s) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(r->out, d_out, seq * sizeof(float), cudaMemcpyDeviceToHost, s) == cudaSuccess;
     if (ok && r->primal)
         ok = cudaMemcpyAsync(r->primal, d_pr, (size_t)c.N * c.J * sizeof(float), cudaMemcpyDeviceToHost, s) ==
@@ -231,6 +242,14 @@ void Server::retire(int slot)
     Controller &c = ctrls[r->ctrl];
     c.busy = false;
     arena.release(r->off, r->bytes);
+    if (r->state.load() == Q_DONE && slot_flag[slot] != 0) {
+        // a bounded device-side wait of the solve ran out: the outputs and the
+        // exported multiplier are invalid, so the controller starts cold next
+        r->state.store(Q_FAILED);
+        r->fail_status = PRISM_ERR_TIMEOUT;
+        last_error = "a device-side wait of the solve ran out its bound";
+        c.has_state = false;
+    }
     const int st = r->state.load();
     if (st == Q_DONE) {
         const double ms = (r->t_done - r->t_submit) * 1e3;
@@ -301,7 +320,11 @@ void Server::run()
                 if (ok[k]) {
                     if (jobs[k].c.warm) ctrls[r.ctrl].has_state = true;
                 } else {
+                    // the multiplier may already be shifted or partly written:
+                    // the controller's next request starts cold
+                    ctrls[r.ctrl].has_state = false;
                     last_error = err;
+                    r.fail_status = PRISM_ERR_CUDA;
                     r.t_done = now_s();
                     r.state.store(Q_FAILED);
                 }
@@ -335,12 +358,20 @@ prism_status prism_server_create(size_t mem_budget_bytes, int max_inflight, doub
                      cudaGetErrorString(e));
     }
     S.arena.init(base, mem_budget_bytes);
+    e = cudaHostAlloc(reinterpret_cast<void **>(&S.slot_flag), sizeof(int) * max_inflight, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        delete ps;
+        return sfail(PRISM_ERR_OOM, "server flags: %s", cudaGetErrorString(e));
+    }
+    std::memset(S.slot_flag, 0, sizeof(int) * max_inflight);
     S.streams.resize(max_inflight);
     S.slot_req.resize(max_inflight);
     for (int k = 0; k < max_inflight; ++k) {
         e = cudaStreamCreateWithFlags(&S.streams[k], cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             for (int q = 0; q < k; ++q) cudaStreamDestroy(S.streams[q]);
+            cudaFreeHost(S.slot_flag);
             cudaFree(base);
             delete ps;
             return sfail(PRISM_ERR_CUDA, "server streams: %s", cudaGetErrorString(e));
@@ -441,7 +472,9 @@ prism_status prism_server_wait(prism_server_t ps, unsigned long long ticket, dou
     if (state) *state = s;
     if (latency_ms) *latency_ms = (s == Q_DONE || s == Q_DROPPED) ? (r->t_done - r->t_submit) * 1e3 : -1.0;
     if (pred()) S.tickets.erase(ticket);
-    if (s == Q_FAILED) return sfail(PRISM_ERR_CUDA, "request failed: %s", S.last_error.c_str());
+    if (s == Q_FAILED)
+        return sfail(r->fail_status == PRISM_ERR_TIMEOUT ? PRISM_ERR_TIMEOUT : PRISM_ERR_CUDA, "request failed: %s",
+                     S.last_error.c_str());
     return PRISM_OK;
 }
 
@@ -497,6 +530,7 @@ prism_status prism_server_destroy(prism_server_t ps)
     S.cv.notify_all();
     if (S.th.joinable()) S.th.join();
     for (cudaStream_t s : S.streams) cudaStreamDestroy(s);
+    cudaFreeHost(S.slot_flag);
     cudaFree(S.arena.base);
     delete ps;
     return PRISM_OK;

@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
             L.prism_diag_wait_timeout.restype = i
             L.prism_test_fail_allocs.argtypes = [i, i]
             L.prism_test_fail_allocs.restype = None
+            L.prism_test_set_device_flag.argtypes = [P, i]
+            L.prism_test_set_device_flag.restype = i
             for name in ("create", "factor", "solve", "solve_ex", "solve_plain", "solve_host",
                          "check_fp64", "shift_state", "get_factor", "query", "device_status", "destroy"):
                 getattr(L, "prism_proj_" + name).restype = i
@@ -473,6 +475,12 @@ def test_fail_allocs(skip: int, count: int) -> None:
     """prism_test_fail_allocs: after ``skip`` device allocations of the library, fail
     the next ``count`` as out-of-memory (host-side fault injection; (0, 0) = off)."""
     lib().prism_test_fail_allocs(int(skip), int(count))
+
+
+def test_set_device_flag(proj: "Projector", value: int = 1) -> None:
+    """prism_test_set_device_flag: write the handle's device-side timeout flag from
+    the host (what a solve whose bounded wait ran out leaves behind)."""
+    _check(lib().prism_test_set_device_flag(proj._h, int(value)))
 
 
 def diag_wait_timeout(poll_limit: int = 1000) -> bool:

@@ -88,3 +88,21 @@ def test_plan_rejects_bad_problems():
         pp.Plan([item], 10)
     assert e.value.status == 2
     P.close()
+
+
+def test_autotune_reports_a_flag_raised_on_any_problem():
+    """Autotuning reads the timeout flag of every distinct handle (the launches
+    write each tile's flag to its own problem's handle).  A flag written from
+    the host on the LAST problem's handle fails plan creation with
+    PRISM_ERR_TIMEOUT and is cleared; the next creation succeeds."""
+    iters = 10
+    items, _ = make_items(iters, seed=3)
+    pp.test_set_device_flag(items[-1]["proj"], 1)
+    with pytest.raises(pp.PrismError) as e:
+        pp.Plan(items, iters, autotune=True)
+    assert e.value.status == 8
+    plan = pp.Plan(items, iters, autotune=True)
+    plan.close()
+    for it in items:
+        it["proj"].device_status()
+        it["proj"].close()

@@ -116,3 +116,38 @@ def test_admission_and_supersede():
     assert st["completed"] + st["dropped"] == 3
     S.close()
     P.close()
+
+
+def test_timed_out_request_is_failed_and_next_starts_cold():
+    """A request whose solve left the handle's timeout flag set is reported
+    failed (PRISM_ERR_TIMEOUT), never done; the controller's next request
+    starts from a zero multiplier.  The flag is written from the host (what a
+    bounded device-side wait that ran out leaves behind): no device fault."""
+    import torch
+    J, H, N, dt, prec = CTRLS["C"]
+    d = controller_data("C", 3)
+    P = pp.Projector(J, H, dt, d[0]["bounds"]).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, prec)
+    S = pp.Server(mem_budget_bytes=1 << 28, max_inflight=2)
+    cid = S.add_controller(P, N, ITERS, warm=True)
+    out0 = np.empty((N, H, J), np.float32)
+    assert S.wait(S.submit(cid, d[0]["q0"], d[0]["v0"], d[0]["xi"], out0))[0] == "done"
+    pp.test_set_device_flag(P, 1)
+    out1 = np.empty((N, H, J), np.float32)
+    t1 = S.submit(cid, d[1]["q0"], d[1]["v0"], d[1]["xi"], out1)
+    with pytest.raises(pp.PrismError) as e:
+        S.wait(t1)
+    assert e.value.status == 8          # PRISM_ERR_TIMEOUT
+    out2 = np.empty((N, H, J), np.float32)
+    assert S.wait(S.submit(cid, d[2]["q0"], d[2]["v0"], d[2]["xi"], out2))[0] == "done"
+    st = S.stats()
+    assert st["completed"] == 2 and st["failed"] == 1
+    S.close()
+    # the flag was consumed by the failed request; the third started cold
+    P.device_status()
+    xi = torch.from_numpy(d[2]["xi"]).cuda()
+    q0 = torch.from_numpy(d[2]["q0"]).cuda()
+    v0 = torch.from_numpy(d[2]["v0"]).cuda()
+    x, _, _, _ = P.solve_ex(q0, v0, xi, ITERS, want_dual_out=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(x.cpu().numpy(), out2)
+    P.close()
