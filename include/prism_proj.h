@@ -242,7 +242,9 @@ prism_status prism_proj_get_factor(prism_proj_t h, double *K_host, double *kb_ho
 
 /*
  * prism_proj_query -- launch facts of the solve kernel for this handle:
- *   out[0] columns per tile, out[1] samples per tile, out[2] thread blocks per
+ *   out[0] columns per tile, out[1] samples per tile (0: the tiles are runs
+ *   of flattened columns n*J + j, as for the ADMM iteration on the tensor
+ *   cores, not whole samples), out[2] thread blocks per
  *   SM, out[3] persistent grid size for batch, out[4] dynamic shared memory
  *   bytes per block, out[5] registers per thread, out[6] per-thread horizon
  *   chunk (the kernel variant), out[7] number of SMs.

@@ -169,7 +169,7 @@ struct prism_proj_s {
     float *d_Kt32 = nullptr;             // [n][MP] transposed K, FP32, zero padded
     float *d_kb32 = nullptr;             // [MP]
     float *d_wp = nullptr;               // [PRISM_MAX_H] position-row weights
-    float *d_Khi = nullptr, *d_Klo = nullptr;   // [n+4][n+1] tf32 split of [K' | kb'] + quarter-prefix rows
+    float *d_Khi = nullptr, *d_Klo = nullptr;   // [n+4][n+4] tf32 split of [K' | kb' | C] + quarter-prefix rows
     int *d_err = nullptr;                // tensor-core wait timeout flag
     double *d_wfull = nullptr;           // factor input: per-row weights (4 blocks x H)
     // plain comparator workspace
@@ -258,14 +258,31 @@ __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wr
         const int j = e / MP, i = e % MP;
         Kt32[e] = (i < n) ? (float)K64[i * n + j] : 0.0f;
     }
-    // tf32 split of [K' | kb'] (n x (n+1)) for the tensor-core K-apply: hi = the
-    // entry rounded to tf32, lo = the remainder in FP32 (the tensor core keeps its
-    // leading tf32 bits).
+    // tf32 split of [K' | kb' | C] (n x (n+4), row stride KW = n + 4) for the
+    // tensor-core K-apply: hi = the entry rounded to tf32, lo = the remainder in
+    // FP32 (the tensor core keeps its leading tf32 bits).  C has three columns:
+    // C[i][b-1] = sum_{c <= min(b*hq, H) - 2} K'[i][c], the response of x_{i+1}
+    // to one unit added to the right-hand side of every unknown before quarter
+    // b (time steps 1 .. b*hq - 1); the solve feeds each quarter's total of the
+    // position-row terms of F^T through it (L^T is a suffix sum).
     __syncthreads();
-    for (int e = tid; e < n * (n + 1); e += nth) {
+    // C by running sums along each row of K' (the shared factor is no longer needed)
+    double *Cs = Bs;   // [n][3]
+    for (int i = tid; i < n; i += nth) {
+        double run = 0.0;
+        int cc = 0;
+        for (int bq = 1; bq <= 3; ++bq) {
+            const int cend = min(bq * hq, H) - 2;
+            for (; cc <= cend; ++cc) run += K64[i * n + cc];
+            Cs[i * 3 + bq - 1] = run;
+        }
+    }
+    __syncthreads();
+    const int KW = n + 4;
+    for (int e = tid; e < n * KW; e += nth) {
         uint32_t r;
-        const int i = e / (n + 1), j = e - i * (n + 1);
-        const double kv = (j < n) ? K64[i * n + j] : kb64[i];
+        const int i = e / KW, j = e - i * KW;
+        const double kv = (j < n) ? K64[i * n + j] : (j == n) ? kb64[i] : Cs[i * 3 + (j - n - 1)];
         const float kf = (float)kv;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(kf));
         const float hi = __uint_as_float(r);
@@ -274,19 +291,20 @@ __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wr
     }
     // Rows n + b (b = 0..3): the sum of x over the time steps before quarter b of
     // the tensor-core kernel (quarters of hq steps), x_0 = v0 included, as the
-    // same linear map of [rhs | v0]: sum_{1 <= i < b*hq, i <= n} [K' | kb'][i-1]
-    // plus 1 on v0 when b >= 1.
-    for (int e = tid; e < 4 * (n + 1); e += nth) {
-        const int bq = e / (n + 1), j = e - bq * (n + 1);
+    // same linear map of [rhs | v0 | quarter totals]: the sum of rows i - 1 of
+    // [K' | kb' | C] over 1 <= i < b*hq, i <= n, plus 1 on v0 when b >= 1.
+    for (int e = tid; e < 4 * KW; e += nth) {
+        const int bq = e / KW, j = e - bq * KW;
         const int iend = min(bq * hq - 1, n);
         double acc = (j == n && bq >= 1) ? 1.0 : 0.0;
-        for (int i = 1; i <= iend; ++i) acc += (j < n) ? K64[(i - 1) * n + j] : kb64[i - 1];
+        for (int i = 1; i <= iend; ++i)
+            acc += (j < n) ? K64[(i - 1) * n + j] : (j == n) ? kb64[i - 1] : Cs[(i - 1) * 3 + (j - n - 1)];
         uint32_t r;
         const float kf = (float)acc;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(kf));
         const float hi = __uint_as_float(r);
-        Khi32[(n + bq) * (n + 1) + j] = hi;
-        Klo32[(n + bq) * (n + 1) + j] = (float)(acc - (double)hi);
+        Khi32[(n + bq) * KW + j] = hi;
+        Klo32[(n + bq) * KW + j] = (float)(acc - (double)hi);
     }
 }
 
@@ -295,6 +313,7 @@ __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wr
 // ===========================================================================
 struct SolveParams {
     int N, J, H, n, MP, iters, T, ntiles;
+    int flat;                            // tiles of CMAX flattened columns (solve_kernel_z) instead of T samples
     float rho;
     double dt;
     float wv, wa0, wa, wj0, wj;
@@ -305,8 +324,8 @@ struct SolveParams {
     const float *__restrict__ Kt;        // [n][MP]
     const float *__restrict__ kb;        // [MP]
     const float *__restrict__ wp;        // [>= H]
-    const float *__restrict__ Khi;       // [n+4][n+1] tf32 high part of [K' | kb'] and the quarter-prefix rows
-    const float *__restrict__ Klo;       // [n+4][n+1] remainder - Khi
+    const float *__restrict__ Khi;       // [n+4][n+4] tf32 high part of [K' | kb' | C] and the quarter-prefix rows
+    const float *__restrict__ Klo;       // [n+4][n+4] remainder - Khi
     int *err;                            // set to 1 if a tensor-core wait ran out
     const float *x_init;                 // [N][H][J] warm-start iterate or NULL (x^0 = xi)
     const float *dual_init;              // [N][D][J] warm-start multiplier or NULL (0)
@@ -547,6 +566,15 @@ __device__ __forceinline__ float tf32_rna(float v)
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
     return __uint_as_float(r);
+}
+
+// The tf32 value nearest to a finite float, ties away from zero (as cvt.rna.tf32
+// for finite inputs): add half a tf32 unit to the magnitude bits and clear the
+// 13 bits below the tf32 mantissa (a carry into the exponent is the right
+// result).  Two integer instructions.
+__device__ __forceinline__ float tf32_round(float v)
+{
+    return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
@@ -860,7 +888,7 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     const bool v0col = kq == HQ;
                     const int j = v0col ? n : xk - 1;           // its column of [K' | kb']
                     const bool in = (prefix || (xt >= 1 && xt <= n)) && (v0col || (rr < HQ && xk >= 1 && xk <= n));
-                    const int src = i * (n + 1) + j;
+                    const int src = i * (n + 4) + j;
                     *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, kq, KD)) =
                         in ? (low ? p.Klo[src] : p.Khi[src]) : 0.0f;
                 }
@@ -1290,6 +1318,608 @@ solve_kernel(const __grid_constant__ LaunchParams P)
 }
 
 // ===========================================================================
+// Paired FP32 arithmetic of sm_100 and later: one instruction on a float2 (two
+// rows), each component rounded exactly as the scalar operation.
+// ===========================================================================
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, rounded once (fma(b, -1, a))
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 clamp2(float2 v, float lox, float hix, float loy, float hiy)
+{
+    return make_float2(clampf(v.x, lox, hix), clampf(v.y, loy, hiy));
+}
+// Row r of a per-thread array of row pairs (r known at compile time after unrolling).
+template <int NP>
+__device__ __forceinline__ float &rowof(float2 (&a)[NP], int r)
+{
+    return (r & 1) ? a[r >> 1].y : a[r >> 1].x;
+}
+
+// This quarter-thread's x (KN - 1 time steps) and its prefix sum (index KN - 1)
+// from the accumulator: time step k sits in D columns 4k + t%4 (products with
+// the high parts of B) and ND + 4k + t%4 (low parts), lanes t/4 (high parts of
+// the right-hand side) and t/4 + 8 (its remainders); a 16x128b.x4 load at
+// column 16g hands thread t, in registers 2m and 2m + 1, both lanes of column
+// 16g + 4m + t%4.  The four partial products are summed as one paired add of
+// (lane t/4, lane t/4 + 8) over the two halves of D and one add of the pair.
+// Without the split only the first of them exists.
+template <int KN, int ND>
+__device__ __forceinline__ void tmem_read_x(uint32_t taddr, bool split, float out[KN])
+{
+    constexpr int NL = (KN + 3) / 4;
+#pragma unroll
+    for (int g0 = 0; g0 < NL; g0 += 2) {
+        uint32_t h[2][8], q[2][8];
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            if (g0 + g < NL) {
+                asm volatile("tcgen05.ld.sync.aligned.16x128b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                             : "=r"(h[g][0]), "=r"(h[g][1]), "=r"(h[g][2]), "=r"(h[g][3]), "=r"(h[g][4]),
+                               "=r"(h[g][5]), "=r"(h[g][6]), "=r"(h[g][7])
+                             : "r"(taddr + (uint32_t)(16 * (g0 + g))));
+                if (split) {
+                    asm volatile("tcgen05.ld.sync.aligned.16x128b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                                 : "=r"(q[g][0]), "=r"(q[g][1]), "=r"(q[g][2]), "=r"(q[g][3]), "=r"(q[g][4]),
+                                   "=r"(q[g][5]), "=r"(q[g][6]), "=r"(q[g][7])
+                                 : "r"(taddr + (uint32_t)(ND + 16 * (g0 + g))));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) q[g][e] = 0u;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) h[g][e] = q[g][e] = 0u;
+            }
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(h[0][0]), "+r"(h[0][1]), "+r"(h[0][2]), "+r"(h[0][3]), "+r"(h[0][4]), "+r"(h[0][5]), "+r"(h[0][6]), "+r"(h[0][7]), "+r"(h[1][0]), "+r"(h[1][1]), "+r"(h[1][2]), "+r"(h[1][3]), "+r"(h[1][4]), "+r"(h[1][5]), "+r"(h[1][6]), "+r"(h[1][7]),
+                       "+r"(q[0][0]), "+r"(q[0][1]), "+r"(q[0][2]), "+r"(q[0][3]), "+r"(q[0][4]), "+r"(q[0][5]), "+r"(q[0][6]), "+r"(q[0][7]), "+r"(q[1][0]), "+r"(q[1][1]), "+r"(q[1][2]), "+r"(q[1][3]), "+r"(q[1][4]), "+r"(q[1][5]), "+r"(q[1][6]), "+r"(q[1][7])
+                     :: "memory");
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int k = 4 * (g0 + g) + m;
+                if (k < KN) {
+                    if (split) {
+                        const float2 s = add2(make_float2(__uint_as_float(h[g][2 * m]), __uint_as_float(h[g][2 * m + 1])),
+                                              make_float2(__uint_as_float(q[g][2 * m]), __uint_as_float(q[g][2 * m + 1])));
+                        out[k] = s.x + s.y;
+                    } else {
+                        out[k] = __uint_as_float(h[g][2 * m]);
+                    }
+                }
+            }
+    }
+}
+
+// Shared-memory carve-up of solve_kernel_z (byte offsets).
+struct ZSmem {
+    int a, bhi, xi, wt, total;
+};
+
+// Words between two quarter-threads' xi rows: the row pairs rounded up to an odd
+// count, so the 64-bit loads of a half-warp hit 32 distinct banks.
+__host__ __device__ constexpr int z_xi_stride(int hq) { return 2 * (((hq + 1) / 2) | 1); }
+
+__host__ __device__ inline ZSmem solve_smem_z(int hq)
+{
+    const int KD = tc_kd(hq), ND = tc_nrows(hq), NP = (hq + 1) / 2;
+    ZSmem L;
+    int off = 0;
+    L.a = off;   off += 128 * KD * 4;                   // A operand; the tile slab outside the iteration
+    L.bhi = off; off += 2 * ND * KD * 4;                // B: high parts over low parts (N-stacked)
+    L.xi = off;  off += NTHREADS * z_xi_stride(hq) * 4; // xi, each quarter-thread's rows contiguous
+    L.wt = off;  off += 3 * 4 * NP * 8;                 // weight pairs: position, acceleration, jerk x quarter x pair
+    L.total = off;
+    return L;
+}
+
+// ===========================================================================
+// K3 (default path): the persistent ADMM solve with the K-apply on the tensor
+// cores.  Same tile, quarter and tensor-memory layout as solve_kernel<TC>, but
+// the iteration is carried in the form
+//   y = Fh x^l;  w = 2 y + m;  z = clip(w, lo, hi);  m <- (w - y) - z
+//   x^{l+1} = K' (xi - rho Fh^T W m) + kb' v0
+// with m^{l+1} = u^l - z^{l+1} (u the scaled multiplier, u^{l+1} = m^{l+1} + y^{l+1}),
+// i.e. the slack clip, the x-step with right-hand side xi + rho Fh^T W (z - u)
+// and the multiplier update of the oracle, in the same order.  Every operation
+// on the rows is done two rows at a time with the paired FP32 instructions,
+// and the part of the position suffix sum (L^T) that crosses quarters reaches
+// x through the MMA: quarter b >= 1 writes -rho times its total into its spare
+// K slot, which meets the columns C of [K' | kb' | C].  (Carrying x^l as the
+// base instead of xi, which the x-step's optimality condition allows in exact
+// arithmetic, lets the rounding of each K-apply shift the problem being solved:
+// measured 2.3e-4 against the oracle after 100 iterations.)
+// ===========================================================================
+template <int HQ, bool BATCHED>
+__global__ void __launch_bounds__(NTHREADS, solve_min_blocks<HQ>())
+solve_kernel_z(const __grid_constant__ LaunchParams P)
+{
+    constexpr int HP = 4 * HQ;
+    constexpr int CP = col_stride(HQ);
+    constexpr int TMEM_COLS = tc_tmem_cols(HQ);
+    constexpr int KD = tc_kd(HQ), ND = tc_nrows(HQ), HQ4 = tc_hq4(HQ);
+    constexpr int NP = (HQ + 1) / 2;   // row pairs; the second row of the last pair is a spare
+    static_assert(HQ & 1, "row pairs assume an odd horizon chunk (one spare row)");
+    static_assert(tc_nrows(HQ) + 16 * ((HQ + 1 + 3) / 4) <= tc_tmem_cols(HQ),
+                  "the readback reads past the tensor-memory allocation");
+    static_assert((4 * HQ + 2) * col_stride(HQ) <= 128 * tc_kd(HQ), "the tile slab must fit in the A operand");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mma_bar;
+    const ZSmem L = solve_smem_z(HQ);
+    unsigned char *As = smem_raw + L.a;
+    float *xs = reinterpret_cast<float *>(smem_raw + L.a);   // tile slab, outside the iteration loop only
+
+    const float2 *wtab = reinterpret_cast<const float2 *>(smem_raw + L.wt);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int c = tid >> 2;       // column in tile
+    const int b = tid & 3;        // time quarter
+    const int i0 = b * HQ;
+    constexpr int SX = z_xi_stride(HQ);
+    float *xit = reinterpret_cast<float *>(smem_raw + L.xi) + tid * SX;   // this thread's xi rows
+    const float2 *xit2 = reinterpret_cast<const float2 *>(xit);
+    // A rows of this column (see solve_kernel): high parts, remainders 8 below
+    const int arow_hi = 32 * (warp & 3) + 16 * (warp >> 2) + (lane >> 2);
+    // local row r goes to word (r & 3) ^ b of 16-byte slot r >> 2 of this quarter's K block
+    float *ahi = reinterpret_cast<float *>(As + cm_off(arow_hi, HQ4 * b, KD));
+    constexpr int LO = 8 * KD;   // floats from a column's high row to its low row
+    float *aw[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) aw[m] = ahi + (m ^ b);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tmem_slot)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mma_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = tmem_slot;
+    uint32_t mma_phase = 0;
+    bool aborted = false, timed_out = false;
+    int cur = -1;
+    const float2 TWO = make_float2(2.0f, 2.0f);
+
+    for (int tile = blockIdx.x; tile < P.ntiles && !aborted; tile += gridDim.x) {
+        int pi = 0;
+        if (BATCHED) {
+            int lo = 0, hi = P.nprob - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (P.many[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+            }
+            pi = lo;
+        }
+        const SolveParams &p = BATCHED ? P.many[pi] : P.one;
+        const int H = p.H, J = p.J, n = p.n;
+        const int HJ = H * J;
+        const float rho = p.rho;
+        const int iters = p.iters, polish = p.polish;
+        // the tile: flattened columns [C0, C0 + Ct) of the batch (column n*J + j is joint j of sample n)
+        const int C0 = (tile - p.tile0) * CMAX;
+        const int Ct = min(CMAX, p.N * J - C0);
+        __syncthreads();   // previous tile fully stored before the slab is overwritten
+        if (pi != cur) {
+            // per-problem operand B = [K' | kb' | C] split in tf32 high / low parts
+            // (rows = D columns in the interleaved output order, then the four
+            // quarter-prefix rows; K = this problem's right-hand-side slots, v0 in
+            // quarter 0's spare slot, the quarter totals in the others') and the
+            // weight pairs (zero on rows that do not exist)
+            const int KW = n + 4;
+            for (int e = tid; e < 2 * ND * KD; e += NTHREADS) {
+                const int pr = e / KD, kq = e - pr * KD;
+                const bool low = pr >= ND;
+                const int pc = low ? pr - ND : pr;
+                const int xt = (pc & 3) * HQ + (pc >> 2);   // time step of D column pc
+                const bool prefix = pc >= 4 * HQ;           // column 4HQ + b: quarter b's prefix sum
+                const int i = prefix ? n + (pc & 3) : xt - 1;
+                const int kb_ = kq / HQ4, kr = kq - kb_ * HQ4;
+                const int rr = (kr & ~3) | ((kr & 3) ^ kb_);  // local row stored in this slot
+                const int xk = kb_ * HQ + rr;
+                int j = -1;
+                if (rr < HQ) j = (xk >= 1 && xk <= n) ? xk - 1 : -1;
+                else if (rr == HQ) j = (kb_ == 0) ? n : n + kb_;
+                const bool in = (prefix || (xt >= 1 && xt <= n)) && j >= 0;
+                const int src = i * KW + j;
+                *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, kq, KD)) =
+                    in ? (low ? p.Klo[src] : p.Khi[src]) : 0.0f;
+            }
+            float *wt = reinterpret_cast<float *>(smem_raw + L.wt);
+            for (int e = tid; e < 3 * 8 * NP; e += NTHREADS) {
+                const int kind = e / (8 * NP), rem = e - kind * 8 * NP;
+                const int bq = rem / (2 * NP), r = rem - bq * 2 * NP;
+                const int i = bq * HQ + r;
+                const bool ex = r < HQ && i < H;
+                float w = 0.0f;
+                if (kind == 0) w = ex ? p.wp[i] : 0.0f;
+                else if (kind == 1) w = ex ? (i == 0 ? p.wa0 : p.wa) : 0.0f;
+                else w = (ex && i >= 1) ? (i == 1 ? p.wj0 : p.wj) : 0.0f;
+                wt[e] = w;
+            }
+            cur = pi;
+        }
+        // ---- a1: the tile's columns of xi (or x_init, or the drawn samples) into rows 2..H+1
+        for (int e = tid; e < (HP + 2) * CP; e += NTHREADS) xs[e] = 0.0f;
+        __syncthreads();
+        if (p.s_mean) {
+            // the samples covering the tile are contiguous in the batch: draw them by
+            // counter blocks of 4 and keep the tile's columns
+            const int nf = C0 / J, nl_ = (C0 + Ct - 1) / J;
+            const unsigned long long e0 = (unsigned long long)nf * HJ;
+            const unsigned long long e1 = (unsigned long long)(nl_ + 1) * HJ;
+            const unsigned long long q0b = e0 >> 2, q1b = (e1 + 3) >> 2;
+            for (unsigned long long q = q0b + tid; q < q1b; q += NTHREADS) {
+                float z[4];
+                normals4(q, p.seed, p.sstream, z);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned long long e = 4 * q + u;
+                    if (e < e0 || e >= e1) continue;
+                    const int nn = (int)(e / HJ), rem = (int)(e - (unsigned long long)nn * HJ);
+                    const int k = rem / J, j = rem - k * J;
+                    const int cc = nn * J + j - C0;
+                    if (cc < 0 || cc >= Ct) continue;
+                    const float v = fmaf(p.s_std[rem], z[u], p.s_mean[rem]);
+                    xs[(k + 2) * CP + cc] = v;
+                    if (p.xi_out) p.xi_out[e] = v;
+                }
+            }
+        } else {
+            const float *src = p.x_init ? p.x_init : p.xi;
+            const int total = Ct * H;
+            for (int e = tid; e < total; e += NTHREADS) {
+                const int k = e / Ct, cc = e - k * Ct;
+                const int col = C0 + cc, nn = col / J, j = col - nn * J;
+                xs[(k + 2) * CP + cc] = __ldg(src + ((size_t)nn * H + k) * J + j);
+            }
+        }
+        __syncthreads();
+        // ---- a2: bounds, x^0 (x_0 := v0), the halo and the prefix over earlier quarters
+        const bool colv = c < Ct;
+        const int n_c = colv ? (C0 + c) / J : 0;      // sample and joint of this column
+        const int jj = colv ? (C0 + c) - n_c * J : 0;
+        const float q0j = p.q0[jj], v0j = p.v0[jj];
+        const ColBounds cb = col_bounds(p.bounds, J, jj, p.dt, q0j, v0j);
+        // rows with shifted bounds: acceleration row 0 and jerk row 1 of quarter 0
+        const float alo_r0 = (b == 0) ? cb.alo0 : cb.alo, ahi_r0 = (b == 0) ? cb.ahi0 : cb.ahi;
+        const float jlo_r1 = (b == 0) ? cb.jlo1 : cb.jlo, jhi_r1 = (b == 0) ? cb.jhi1 : cb.jhi;
+        if (b == 0) xs[2 * CP + c] = colv ? v0j : 0.0f;
+        float2 X[NP];   // rows of this quarter; the spare slot holds the sum of x over earlier quarters
+        float h0, h1;   // x_{i0-2}, x_{i0-1}
+        {
+            float run = 0.0f;
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) {
+                rowof(X, r) = (r == 0 && b == 0) ? (colv ? v0j : 0.0f) : xs[(i0 + r + 2) * CP + c];
+                run += rowof(X, r);
+            }
+            h0 = xs[i0 * CP + c];
+            h1 = (b == 0) ? 0.0f : xs[(i0 + 1) * CP + c];
+            rowof(X, HQ) = excl_prefix4(run, b);
+        }
+        // y = Fh x on this quarter's rows: the position prefix, first and second differences
+        const auto rows_y = [&](float2 (&Yp)[NP], float2 (&Ya)[NP], float2 (&Yj)[NP]) {
+            float cs = rowof(X, HQ), xm1 = h1, am1 = h1 - h0;
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) {
+                const float xr = rowof(X, r);
+                cs += xr;
+                const float ya = xr - xm1;
+                rowof(Yp, r) = cs;
+                rowof(Ya, r) = ya;
+                rowof(Yj, r) = ya - am1;
+                xm1 = xr;
+                am1 = ya;
+            }
+            rowof(Yp, HQ) = 0.0f;
+            rowof(Ya, HQ) = 0.0f;
+            rowof(Yj, HQ) = 0.0f;
+        };
+        // ---- xi of this thread's rows (the slab holds x_init instead when one is given)
+        {
+            const float *xisrc = p.xi + (size_t)n_c * HJ + jj;
+#pragma unroll
+            for (int r = 0; r < 2 * NP; ++r) {
+                float v = 0.0f;
+                if (r < HQ && colv && i0 + r < H) v = p.x_init ? __ldg(xisrc + (size_t)(i0 + r) * J) : xs[(i0 + r + 2) * CP + c];
+                xit[r] = v;
+            }
+        }
+        // ---- u^0 of row i of kind k (0 velocity, 1 position, 2 acceleration, 3 jerk) in the
+        // device units: the warm-start multiplier u' (the oracle's units, unit rows) / sqrt(w)
+        const size_t dbase = (size_t)n_c * p.D * J + jj;
+        const auto u0 = [&](int kind, int i) -> float {
+            if (!p.dual_init || !colv || i >= H) return 0.0f;
+            if (kind == 0) return __ldg(p.dual_init + dbase + (size_t)i * J) * rsqrtf(p.wv);
+            if (kind == 1) return __ldg(p.dual_init + dbase + (size_t)(H + i) * J) * rsqrtf(p.wp[i]);
+            if (kind == 2) return __ldg(p.dual_init + dbase + (size_t)(2 * H + i) * J) * rsqrtf(i == 0 ? p.wa0 : p.wa);
+            if (i < 1) return 0.0f;
+            return __ldg(p.dual_init + dbase + (size_t)(3 * H + i - 1) * J) * rsqrtf(i == 1 ? p.wj0 : p.wj);
+        };
+        // ---- initial multiplier state m = u^0 - y^0 (0 on rows that do not exist)
+        float2 Mv[NP], Mp[NP], Ma[NP], Mj[NP];
+        {
+            float2 Yp[NP], Ya[NP], Yj[NP];
+            rows_y(Yp, Ya, Yj);
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) {
+                const int i = i0 + r;
+                const bool vi = colv && i < H;
+                rowof(Mv, r) = vi ? u0(0, i) - rowof(X, r) : 0.0f;
+                rowof(Mp, r) = vi ? u0(1, i) - rowof(Yp, r) : 0.0f;
+                rowof(Ma, r) = vi ? u0(2, i) - rowof(Ya, r) : 0.0f;
+                rowof(Mj, r) = (vi && i >= 1) ? u0(3, i) - rowof(Yj, r) : 0.0f;
+            }
+            rowof(Mv, HQ) = rowof(Mp, HQ) = rowof(Ma, HQ) = rowof(Mj, HQ) = 0.0f;
+        }
+        __syncthreads();   // the slab is read: A (which it occupies) is cleared for the MMA
+        for (int e = tid; e < 128 * KD; e += NTHREADS) reinterpret_cast<float *>(As)[e] = 0.0f;
+        __syncthreads();
+        if (b == 0) {
+            // K slot HQ of quarter 0: v0 of this column, split like the right-hand sides
+            const float v = colv ? v0j : 0.0f;
+            const float hi = tf32_rna(v);
+            aw[HQ & 3][32 * (HQ >> 2)] = hi;
+            aw[HQ & 3][32 * (HQ >> 2) + LO] = v - hi;
+        }
+        float dmax = 0.0f;   // max |x^L - x^{L-1}| over this quarter's unknowns
+
+        for (int l = 0; l < iters; ++l) {
+            // ---- a3 slack step, a6 multiplier and a4 g = Fh^T W z, one constraint kind at a time
+            // (two rows per instruction; each kind's z is used as soon as it is formed):
+            //   w = 2 y + m,  z = clip(w, lo, hi),  m <- (w - y) - z
+            //   g_r = z_v,r + P_r + (q_r - q_{r+1}),  q_r = wa z_a,r + (sj_r - sj_{r+1}),  sj = wj z_j,
+            //   P_r = sum over this quarter's rows m >= r of wp z_p,m
+            // (the velocity weight is 1; the next quarter's first sj and q by shuffle; the later
+            // quarters' part of the position sum reaches x through the MMA)
+            // g = Fh^T W m with the updated state (the x-step takes xi - rho g):
+            //   g_r = m_v,r + P_r + (q_r - q_{r+1}),  q_r = wa m_a,r + (sj_r - sj_{r+1}),  sj = wj m_j,
+            //   P_r = sum over this quarter's rows m >= r of wp m_p,m
+            // (the velocity weight is 1; the next quarter's first sj and q by shuffle; the later
+            // quarters' part of the position sum reaches x through the MMA)
+            float2 G[NP];
+            float T;
+            {
+                // position rows (forward prefix of x, slack; then the suffix sum into g)
+                {
+                    float cs = rowof(X, HQ);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        cs += X[k].x;
+                        const float c0 = cs;
+                        if (2 * k + 1 < HQ) cs += X[k].y;
+                        const float2 y = make_float2(c0, (2 * k + 1 < HQ) ? cs : 0.0f);
+                        const float2 w = fma2(TWO, y, Mp[k]);
+                        const float2 z = clamp2(w, cb.plo, cb.phi, cb.plo, cb.phi);
+                        Mp[k] = sub2(sub2(w, y), z);
+                    }
+                    float Pc = 0.0f, Podd = 0.0f;
+#pragma unroll
+                    for (int r = HQ - 1; r >= 0; --r) {
+                        const float2 wp2 = wtab[b * NP + (r >> 1)];
+                        Pc = fmaf((r & 1) ? wp2.y : wp2.x, rowof(Mp, r), Pc);
+                        if (r & 1) Podd = Pc;
+                        else G[r >> 1] = make_float2(Pc, (r + 1 < HQ) ? Podd : 0.0f);
+                    }
+                    T = Pc;
+                }
+                // velocity rows (weight 1)
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    const float2 w = fma2(TWO, X[k], Mv[k]);
+                    const float2 z = clamp2(w, cb.vlo, cb.vhi, cb.vlo, cb.vhi);
+                    Mv[k] = sub2(sub2(w, X[k]), z);
+                    G[k] = add2(G[k], Mv[k]);
+                }
+                // jerk rows: sj = wj m_j, then its first difference toward the future
+                float2 D[NP];
+                {
+                    float xm1 = h1, am1 = h1 - h0;
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        const float a0 = X[k].x - xm1;
+                        const float j0 = a0 - am1;
+                        const float a1 = X[k].y - X[k].x;
+                        const float j1 = a1 - a0;
+                        xm1 = X[k].y;
+                        am1 = a1;
+                        const float2 y = make_float2(j0, (2 * k + 1 < HQ) ? j1 : 0.0f);
+                        const float2 w = fma2(TWO, y, Mj[k]);
+                        const float2 z = (k == 0) ? clamp2(w, cb.jlo, cb.jhi, jlo_r1, jhi_r1)
+                                                  : clamp2(w, cb.jlo, cb.jhi, cb.jlo, cb.jhi);
+                        Mj[k] = sub2(sub2(w, y), z);
+                        D[k] = mul2(wtab[(8 + b) * NP + k], Mj[k]);
+                    }
+                    const float sj_n = from_next4(D[0].x, b);
+#pragma unroll
+                    for (int r = 0; r < HQ; ++r) rowof(D, r) = rowof(D, r) - ((r + 1 < HQ) ? rowof(D, r + 1) : sj_n);
+                }
+                // acceleration rows: q = wa m_a + (first difference of sj), then g += q_r - q_{r+1}
+                {
+                    float xm1 = h1;
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        const float a0 = X[k].x - xm1;
+                        const float a1 = X[k].y - X[k].x;
+                        xm1 = X[k].y;
+                        const float2 y = make_float2(a0, (2 * k + 1 < HQ) ? a1 : 0.0f);
+                        const float2 w = fma2(TWO, y, Ma[k]);
+                        const float2 z = (k == 0) ? clamp2(w, alo_r0, ahi_r0, cb.alo, cb.ahi)
+                                                  : clamp2(w, cb.alo, cb.ahi, cb.alo, cb.ahi);
+                        Ma[k] = sub2(sub2(w, y), z);
+                        D[k] = fma2(wtab[(4 + b) * NP + k], Ma[k], D[k]);
+                    }
+                    const float q_n = from_next4(D[0].x, b);
+#pragma unroll
+                    for (int r = 0; r < HQ; ++r) rowof(D, r) = rowof(D, r) - ((r + 1 < HQ) ? rowof(D, r + 1) : q_n);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) G[k] = add2(G[k], D[k]);
+                }
+            }
+            // ---- right-hand side rhs = xi - rho g -> tf32 high parts (and remainders) in A
+            const bool last = (l == iters - 1);
+            const bool split = l >= iters - polish;
+            float2 RV[NP];
+            {
+                const float2 NRHO2 = make_float2(-rho, -rho);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) RV[k] = fma2(NRHO2, G[k], xit2[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const int r = 2 * k;
+                const float2 hi2 = make_float2(tf32_round(RV[k].x), (r + 1 < HQ) ? tf32_round(RV[k].y) : 0.0f);
+                const float2 lo2 = sub2(RV[k], hi2);
+                aw[r & 3][32 * (r >> 2)] = hi2.x;
+                if (split) aw[r & 3][32 * (r >> 2) + LO] = lo2.x;
+                if (r + 1 < HQ) {
+                    aw[(r + 1) & 3][32 * ((r + 1) >> 2)] = hi2.y;
+                    if (split) aw[(r + 1) & 3][32 * ((r + 1) >> 2) + LO] = lo2.y;
+                }
+            }
+            if (b > 0) {
+                // -rho times this quarter's position total: reaches every earlier time step
+                const float t = -rho * T;
+                const float thi = tf32_round(t);
+                aw[HQ & 3][32 * (HQ >> 2)] = thi;
+                if (split) aw[HQ & 3][32 * (HQ >> 2) + LO] = t - thi;
+            }
+            // A visible to the tensor core, the previous readback of D finished; a warp
+            // whose MMA wait ran out stops the block here
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (__syncthreads_or(timed_out)) {
+                aborted = true;
+                break;
+            }
+            // ---- a5: K-apply, one M = 128 MMA per K-step (as in solve_kernel)
+            if (warp == 0) {
+                const uint32_t idesc = umma_idesc_tf32(128, split ? 2 * ND : round_up(ND, 16));
+                const uint32_t sbo = (uint32_t)(KD >> 2) * 128u;
+                const uint64_t da = umma_desc(smem_addr(As), 128u, sbo);
+                const uint64_t db = umma_desc(smem_addr(smem_raw + L.bhi), 128u, sbo);
+                if (elect_one()) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    for (int ks = 0; ks < (KD >> 3); ++ks) {
+                        const uint64_t kk = (uint64_t)(16 * ks);
+                        umma_tf32(tbase, da + kk, db + kk, idesc, ks > 0 ? 1u : 0u);
+                    }
+                    umma_commit(smem_addr(&mma_bar));
+                }
+                __syncwarp();
+            }
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mma_bar), mma_phase));
+            mma_phase ^= 1u;
+            if (!ok) {
+                timed_out = true;   // X keeps the old iterate; the block stops at the next barrier
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tl = tbase + ((uint32_t)(32 * (warp & 3) + 16 * (warp >> 2)) << 16);
+                float xn[2 * NP];   // rows, then the sum of x over the earlier quarters
+                tmem_read_x<HQ + 1, ND>(tl, split, xn);
+                if (b == 0) xn[0] = colv ? v0j : 0.0f;   // x_0 = v0 exactly
+                if (last) {
+#pragma unroll
+                    for (int r = 0; r < HQ; ++r) {
+                        const int i = i0 + r;
+                        if (i >= 1 && i < H) dmax = fmaxf(dmax, fabsf(xn[r] - rowof(X, r)));
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < NP; ++k) X[k] = make_float2(xn[2 * k], xn[2 * k + 1]);
+                const float s0 = __shfl_up_sync(0xffffffffu, rowof(X, HQ - 2), 1, 4);
+                const float s1 = __shfl_up_sync(0xffffffffu, rowof(X, HQ - 1), 1, 4);
+                h0 = (b > 0) ? s0 : 0.0f;
+                h1 = (b > 0) ? s1 : 0.0f;
+            }
+        }
+        if (__syncthreads_or(aborted || timed_out)) {
+            if (tid == 0 && p.err) atomicExch(p.err, 1);
+            aborted = true;
+        }
+        if (aborted) break;
+
+        // ---- a7: residuals, final multiplier, store
+        float2 Yp[NP], Ya[NP], Yj[NP];
+        rows_y(Yp, Ya, Yj);
+        float viol = 0.0f;
+#pragma unroll
+        for (int r = 0; r < HQ; ++r) {
+            const int i = i0 + r;
+            if (i < H) {
+                const float yv = rowof(X, r), yp = rowof(Yp, r), ya = rowof(Ya, r), yj = rowof(Yj, r);
+                viol = fmaxf(viol, fmaxf(yv - cb.vhi, cb.vlo - yv));
+                viol = fmaxf(viol, fmaxf(yp - cb.phi, cb.plo - yp) * inv_norm_pos(i));
+                const float ea = (i == 0) ? fmaxf(ya - cb.ahi0, cb.alo0 - ya)
+                                          : fmaxf(ya - cb.ahi, cb.alo - ya) * 0.70710678f;
+                viol = fmaxf(viol, ea);
+                if (i >= 1) {
+                    const float ej = (i == 1) ? fmaxf(yj - cb.jhi1, cb.jlo1 - yj) * 0.44721360f
+                                              : fmaxf(yj - cb.jhi, cb.jlo - yj) * 0.40824829f;
+                    viol = fmaxf(viol, ej);
+                }
+            }
+        }
+        if (p.dual_out && colv) {
+            // u^L = m + y^L in the device units -> u' = sqrt(w) u (the oracle's units)
+            const size_t base = (size_t)n_c * p.D * J + jj;
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) {
+                const int i = i0 + r;
+                if (i < H) {
+                    p.dual_out[base + (size_t)i * J] = sqrtf(p.wv) * (rowof(Mv, r) + rowof(X, r));
+                    p.dual_out[base + (size_t)(H + i) * J] = sqrtf(p.wp[i]) * (rowof(Mp, r) + rowof(Yp, r));
+                    p.dual_out[base + (size_t)(2 * H + i) * J] =
+                        sqrtf(i == 0 ? p.wa0 : p.wa) * (rowof(Ma, r) + rowof(Ya, r));
+                    if (i >= 1)
+                        p.dual_out[base + (size_t)(3 * H + i - 1) * J] =
+                            sqrtf(i == 1 ? p.wj0 : p.wj) * (rowof(Mj, r) + rowof(Yj, r));
+                }
+            }
+        }
+        viol = fmaxf(viol, __shfl_xor_sync(0xffffffffu, viol, 1, 4));
+        viol = fmaxf(viol, __shfl_xor_sync(0xffffffffu, viol, 2, 4));
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, 1, 4));
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, 2, 4));
+        if (b == 0 && colv) {
+            const size_t col = (size_t)C0 + c;
+            if (p.primal) p.primal[col] = viol;
+            if (p.dual) p.dual[col] = dmax;
+        }
+        // the final iterate back to the slab (in A, whose last MMA has completed) for a coalesced store
+#pragma unroll
+        for (int r = 0; r < HQ; ++r) xs[(i0 + r + 2) * CP + c] = rowof(X, r);
+        __syncthreads();
+        {
+            const int total = Ct * H;
+            for (int e = tid; e < total; e += NTHREADS) {
+                const int k = e / Ct, cc = e - k * Ct;
+                const int col = C0 + cc, nn = col / J, j = col - nn * J;
+                p.out[((size_t)nn * H + k) * J + j] = xs[(k + 2) * CP + cc];
+            }
+        }
+    }
+    // after a timeout the MMAs of the last commit may still be running: one more
+    // bounded wait for that phase before the tensor memory is freed
+    if (aborted && tid == 0) (void)mbar_wait(smem_addr(&mma_bar), mma_phase ^ 1u);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(TMEM_COLS));
+}
+
+// ===========================================================================
 // K2: plain FP32 comparator.  One thread per column; the iterate, the
 // multiplier rows and the right-hand side live in a workspace laid out
 // [row][column] (coalesced across threads); K is read through the L1 cache.
@@ -1510,11 +2140,13 @@ struct Variant {
     solve_fn b_admm, b_paper, b_admm_tc, b_paper_tc;   // batched launches
 };
 
+// The ADMM iteration with the tensor-core K-apply runs on solve_kernel_z; every
+// other combination on solve_kernel.
 #define VARIANT(HQv)                                                                                    \
     {HQv, solve_kernel<HQv, PRISM_MODE_ADMM, false, false>, solve_kernel<HQv, PRISM_MODE_PAPER, false, false>, \
-     solve_kernel<HQv, PRISM_MODE_ADMM, true, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false>,       \
+     solve_kernel_z<HQv, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false>,                            \
      solve_kernel<HQv, PRISM_MODE_ADMM, false, true>, solve_kernel<HQv, PRISM_MODE_PAPER, false, true>,       \
-     solve_kernel<HQv, PRISM_MODE_ADMM, true, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, true>}
+     solve_kernel_z<HQv, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, true>}
 // prev_variant_hq (used for the rows that always exist) must list the same chunks.
 constexpr int kVariantHQ[] = {3, 5, 7, 9, 11, 13, 15, 17, 21, 25, 29, 33};
 constexpr bool variant_chain_ok()
@@ -1536,13 +2168,15 @@ const Variant *pick_variant(int H)
     return nullptr;
 }
 
-// The tensor-core variant needs its operands in shared memory: up to H = 105.
+// The tensor-core variants need their operands in shared memory (both kernels'
+// layouts must fit): up to H = 116.
 bool tc_fits(int H)
 {
     const Variant *v = pick_variant(H);
     if (!v) return false;
     const int n = H - 1;
-    return solve_smem(v->hq, n, (n + 3) & ~3, true).total <= 220 * 1024 && 2 * tc_nrows(v->hq) <= 256;
+    return solve_smem(v->hq, n, (n + 3) & ~3, true).total <= 220 * 1024 && solve_smem_z(v->hq).total <= 220 * 1024 &&
+           2 * tc_nrows(v->hq) <= 256;
 }
 
 bool is_finite(double v) { return std::isfinite(v); }
@@ -1555,6 +2189,13 @@ prism_status check_handle(prism_proj_t h)
     if (dev != h->device)
         return fail(PRISM_ERR_INVALID_ARG, "current device %d differs from the handle's device %d", dev, h->device);
     return PRISM_OK;
+}
+
+int solve_ntiles(int batch, int J, bool flat)
+{
+    if (flat) return (int)(((long long)batch * J + CMAX - 1) / CMAX);
+    const int T = std::max(1, CMAX / J);
+    return (batch + T - 1) / T;
 }
 
 prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const float *v0,
@@ -1575,7 +2216,10 @@ prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const flo
     const Weights w = make_weights(h->scale, h->dt);
     p.N = batch; p.J = h->J; p.H = h->H; p.n = h->n; p.MP = h->MP; p.iters = iters;
     p.T = std::max(1, CMAX / h->J);
-    p.ntiles = (batch + p.T - 1) / p.T;
+    // the ADMM iteration with the tensor-core K-apply (solve_kernel_z) tiles the
+    // flattened columns; the other kernels tile whole samples
+    p.flat = (h->mode == PRISM_MODE_ADMM && (h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32)) ? 1 : 0;
+    p.ntiles = solve_ntiles(batch, h->J, p.flat != 0);
     p.rho = (float)rho;
     p.dt = h->dt;
     p.wv = (float)w.wv; p.wa0 = (float)w.wa0; p.wa = (float)w.wa; p.wj0 = (float)w.wj0; p.wj = (float)w.wj;
@@ -1613,7 +2257,8 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
     hq = v->hq;
     if (!batched) fn = (mode == PRISM_MODE_ADMM) ? (tc ? v->admm_tc : v->admm) : (tc ? v->paper_tc : v->paper);
     else fn = (mode == PRISM_MODE_ADMM) ? (tc ? v->b_admm_tc : v->b_admm) : (tc ? v->b_paper_tc : v->b_paper);
-    smem = (size_t)solve_smem(v->hq, n_max, MP_max, tc).total;
+    smem = (size_t)((tc && mode == PRISM_MODE_ADMM) ? solve_smem_z(v->hq).total
+                                                    : solve_smem(v->hq, n_max, MP_max, tc).total);
     // The dynamic shared-memory limit is a property of the kernel function, shared
     // by every handle and plan that launches it: only ever raise it.
     cudaFuncAttributes fa;
@@ -1646,8 +2291,7 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
     int hq;
     prism_status st = variant_config(h->H, h->mode, tc, false, h->n, h->MP, h->device, fn, smem, blocks_per_sm, hq);
     if (st) return st;
-    const int T = std::max(1, CMAX / h->J);
-    const int ntiles = (batch + T - 1) / T;
+    const int ntiles = solve_ntiles(batch, h->J, tc && h->mode == PRISM_MODE_ADMM);
     grid = std::max(1, std::min(ntiles, blocks_per_sm * h->num_sms));
     return PRISM_OK;
 }
@@ -1887,8 +2531,8 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
         if (e == cudaSuccess) e = dev_malloc(&kb32, sizeof(float) * std::max(MP, 4));
         if (e == cudaSuccess) e = dev_malloc(&wp, sizeof(float) * PRISM_MAX_H);
         if (e == cudaSuccess) e = dev_malloc(&wfull, sizeof(double) * 4 * H);
-        if (e == cudaSuccess) e = dev_malloc(&Khi, sizeof(float) * (n + 4) * (n + 1));
-        if (e == cudaSuccess) e = dev_malloc(&Klo, sizeof(float) * (n + 4) * (n + 1));
+        if (e == cudaSuccess) e = dev_malloc(&Khi, sizeof(float) * (n + 4) * (n + 4));
+        if (e == cudaSuccess) e = dev_malloc(&Klo, sizeof(float) * (n + 4) * (n + 4));
         if (e == cudaSuccess) e = dev_malloc(&err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
         if (e != cudaSuccess) {
@@ -2222,8 +2866,9 @@ prism_status prism_proj_query(prism_proj_t h, int batch, long long out[8])
     cudaFuncAttributes attr;
     CUDA_TRY(cudaFuncGetAttributes(&attr, (const void *)fn));
     const int T = std::max(1, CMAX / h->J);
-    out[0] = (long long)T * h->J;
-    out[1] = T;
+    const bool flat = h->mode == PRISM_MODE_ADMM && (h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32);
+    out[0] = flat ? CMAX : (long long)T * h->J;
+    out[1] = flat ? 0 : T;   // 0: tiles of flattened columns (not whole samples)
     out[2] = bps;
     out[3] = grid;
     out[4] = (long long)smem;
@@ -2349,20 +2994,49 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
                 if (prec == PRISM_PREC_TF32 || (!g.tc && !tc_fits(probs[k].h->H))) can_switch = false;
             }
             if (can_switch) {
+                // the other kernel tiles the columns differently: its own descriptor table
                 PlanGroup alt = g;
                 alt.tc = !g.tc;
+                alt.d_params = nullptr;
+                const bool flat = alt.tc && alt.mode == PRISM_MODE_ADMM;
+                int tiles = 0;
+                for (SolveParams &sp : alt.params) {
+                    sp.flat = flat ? 1 : 0;
+                    sp.ntiles = solve_ntiles(sp.N, sp.J, flat);
+                    sp.tile0 = tiles;
+                    tiles += sp.ntiles;
+                }
+                alt.lp.ntiles = tiles;
+                if (!alt.params.empty()) alt.lp.one = alt.params[0];
+                cudaError_t e = dev_malloc(&alt.d_params, sizeof(SolveParams) * alt.params.size());
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(alt.d_params, alt.params.data(), sizeof(SolveParams) * alt.params.size(),
+                                   cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) {
+                    cudaFree(alt.d_params);
+                    st = fail(e == cudaErrorMemoryAllocation ? PRISM_ERR_OOM : PRISM_ERR_CUDA, "plan descriptors: %s",
+                              cudaGetErrorString(e));
+                    break;
+                }
+                alt.lp.many = alt.d_params;
                 int hq;
                 int Hmax = 2;
                 for (int k : g.members) Hmax = std::max(Hmax, probs[k].h->H);
                 st = variant_config(Hmax, alt.mode, alt.tc, true, alt.lp.n_max, alt.lp.MP_max, dev, alt.fn, alt.smem,
                                     alt.bps, hq);
-                if (st) break;
                 double ms2 = 0.0;
-                st = plan_time_group(pl, alt, ms2);
-                if (st) break;
+                if (!st) st = plan_time_group(pl, alt, ms2);
+                if (st) {
+                    cudaFree(alt.d_params);
+                    break;
+                }
                 if (ms2 < ms) {
+                    cudaFree(g.d_params);
                     g.tc = alt.tc; g.fn = alt.fn; g.smem = alt.smem; g.bps = alt.bps; g.lp = alt.lp;
+                    g.params = alt.params; g.d_params = alt.d_params;
                     ms = ms2;
+                } else {
+                    cudaFree(alt.d_params);
                 }
             }
             g.tuned_ms = ms;
