@@ -313,7 +313,7 @@ __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wr
 // ===========================================================================
 struct SolveParams {
     int N, J, H, n, MP, iters, T, ntiles;
-    int flat;                            // tiles of CMAX flattened columns (solve_kernel_z) instead of T samples
+    int flat;                            // > 0: tiles of this many flattened columns (solve_kernel_z), else T samples
     float rho;
     double dt;
     float wv, wa0, wa, wj0, wj;
@@ -1404,18 +1404,30 @@ struct ZSmem {
 // count, so the 64-bit loads of a half-warp hit 32 distinct banks.
 __host__ __device__ constexpr int z_xi_stride(int hq) { return 2 * (((hq + 1) / 2) | 1); }
 
-__host__ __device__ inline ZSmem solve_smem_z(int hq)
+// A block of nw warps owns 8 nw columns (four quarter-threads each); its A
+// operand has 16 nw rows (a high and a remainder row per column): M = 128 for
+// eight warps, M = 64 for four.
+__host__ __device__ inline ZSmem solve_smem_z(int hq, int nw)
 {
     const int KD = tc_kd(hq), ND = tc_nrows(hq), NP = (hq + 1) / 2;
     ZSmem L;
     int off = 0;
-    L.a = off;   off += 128 * KD * 4;                   // A operand; the tile slab outside the iteration
-    L.bhi = off; off += 2 * ND * KD * 4;                // B: high parts over low parts (N-stacked)
-    L.xi = off;  off += NTHREADS * z_xi_stride(hq) * 4; // xi, each quarter-thread's rows contiguous
-    L.wt = off;  off += 3 * 4 * NP * 8;                 // weight pairs: position, acceleration, jerk x quarter x pair
+    L.a = off;   off += 16 * nw * KD * 4;                // A operand; the tile slab outside the iteration
+    L.bhi = off; off += 2 * ND * KD * 4;                 // B: high parts over low parts (N-stacked)
+    L.xi = off;  off += 32 * nw * z_xi_stride(hq) * 4;   // xi, each quarter-thread's rows contiguous
+    L.wt = off;  off += 3 * 4 * NP * 8;                  // weight pairs: position, acceleration, jerk x quarter x pair
     L.total = off;
     return L;
 }
+
+// Slab row stride of solve_kernel_z: the block's columns plus 8, so that (odd
+// horizon chunk) the four quarters' rows of a column fall 8 banks apart.
+__host__ __device__ constexpr int z_col_stride(int nw) { return 8 * nw + 8; }
+
+// Resident blocks per SM the kernel is compiled for: 128 registers a thread up
+// to the chunk of 17 steps, 255 beyond.
+template <int HQ, int NW>
+__host__ __device__ constexpr int z_min_blocks() { return NW == 8 ? solve_min_blocks<HQ>() : (HQ <= 17 ? 4 : 2); }
 
 // ===========================================================================
 // K3 (default path): the persistent ADMM solve with the K-apply on the tensor
@@ -1434,23 +1446,27 @@ __host__ __device__ inline ZSmem solve_smem_z(int hq)
 // arithmetic, lets the rounding of each K-apply shift the problem being solved:
 // measured 2.3e-4 against the oracle after 100 iterations.)
 // ===========================================================================
-template <int HQ, bool BATCHED>
-__global__ void __launch_bounds__(NTHREADS, solve_min_blocks<HQ>())
+template <int HQ, int NW, bool BATCHED>
+__global__ void __launch_bounds__(32 * NW, (z_min_blocks<HQ, NW>()))
 solve_kernel_z(const __grid_constant__ LaunchParams P)
 {
+    constexpr int NTH = 32 * NW;        // threads
+    constexpr int CM = 8 * NW;          // columns of a tile
+    constexpr int MROWS = 16 * NW;      // rows of A (the MMA's M)
     constexpr int HP = 4 * HQ;
-    constexpr int CP = col_stride(HQ);
+    constexpr int CP = z_col_stride(NW);
     constexpr int TMEM_COLS = tc_tmem_cols(HQ);
     constexpr int KD = tc_kd(HQ), ND = tc_nrows(HQ), HQ4 = tc_hq4(HQ);
     constexpr int NP = (HQ + 1) / 2;   // row pairs; the second row of the last pair is a spare
     static_assert(HQ & 1, "row pairs assume an odd horizon chunk (one spare row)");
     static_assert(tc_nrows(HQ) + 16 * ((HQ + 1 + 3) / 4) <= tc_tmem_cols(HQ),
                   "the readback reads past the tensor-memory allocation");
-    static_assert((4 * HQ + 2) * col_stride(HQ) <= 128 * tc_kd(HQ), "the tile slab must fit in the A operand");
+    static_assert((4 * HQ + 2) * z_col_stride(NW) <= 16 * NW * tc_kd(HQ), "the tile slab must fit in the A operand");
+    static_assert(NW == 4 || NW == 8, "M = 64 or 128");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mma_bar;
-    const ZSmem L = solve_smem_z(HQ);
+    const ZSmem L = solve_smem_z(HQ, NW);
     unsigned char *As = smem_raw + L.a;
     float *xs = reinterpret_cast<float *>(smem_raw + L.a);   // tile slab, outside the iteration loop only
 
@@ -1464,8 +1480,12 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
     constexpr int SX = z_xi_stride(HQ);
     float *xit = reinterpret_cast<float *>(smem_raw + L.xi) + tid * SX;   // this thread's xi rows
     const float2 *xit2 = reinterpret_cast<const float2 *>(xit);
-    // A rows of this column (see solve_kernel): high parts, remainders 8 below
-    const int arow_hi = 32 * (warp & 3) + 16 * (warp >> 2) + (lane >> 2);
+    // A rows of this column: high parts, remainders 8 below.  D row i sits in
+    // tensor-memory lane i for M = 128 and in lane i % 16 + 32 (i / 16) for M = 64;
+    // a warp reads the 16 lanes from tl_lane of its own lane quarter (warp % 4), and
+    // one 16x128b load hands thread t lanes t/4 and t/4 + 8: both rows of its column.
+    const int arow_hi = (NW == 8) ? 32 * (warp & 3) + 16 * (warp >> 2) + (lane >> 2) : 16 * warp + (lane >> 2);
+    const int tl_lane = (NW == 8) ? 32 * (warp & 3) + 16 * (warp >> 2) : 32 * warp;
     // local row r goes to word (r & 3) ^ b of 16-byte slot r >> 2 of this quarter's K block
     float *ahi = reinterpret_cast<float *>(As + cm_off(arow_hi, HQ4 * b, KD));
     constexpr int LO = 8 * KD;   // floats from a column's high row to its low row
@@ -1507,8 +1527,8 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
         const float rho = p.rho;
         const int iters = p.iters, polish = p.polish;
         // the tile: flattened columns [C0, C0 + Ct) of the batch (column n*J + j is joint j of sample n)
-        const int C0 = (tile - p.tile0) * CMAX;
-        const int Ct = min(CMAX, p.N * J - C0);
+        const int C0 = (tile - p.tile0) * CM;
+        const int Ct = min(CM, p.N * J - C0);
         __syncthreads();   // previous tile fully stored before the slab is overwritten
         if (pi != cur) {
             // per-problem operand B = [K' | kb' | C] split in tf32 high / low parts
@@ -1517,7 +1537,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
             // quarter 0's spare slot, the quarter totals in the others') and the
             // weight pairs (zero on rows that do not exist)
             const int KW = n + 4;
-            for (int e = tid; e < 2 * ND * KD; e += NTHREADS) {
+            for (int e = tid; e < 2 * ND * KD; e += NTH) {
                 const int pr = e / KD, kq = e - pr * KD;
                 const bool low = pr >= ND;
                 const int pc = low ? pr - ND : pr;
@@ -1536,7 +1556,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
                     in ? (low ? p.Klo[src] : p.Khi[src]) : 0.0f;
             }
             float *wt = reinterpret_cast<float *>(smem_raw + L.wt);
-            for (int e = tid; e < 3 * 8 * NP; e += NTHREADS) {
+            for (int e = tid; e < 3 * 8 * NP; e += NTH) {
                 const int kind = e / (8 * NP), rem = e - kind * 8 * NP;
                 const int bq = rem / (2 * NP), r = rem - bq * 2 * NP;
                 const int i = bq * HQ + r;
@@ -1550,7 +1570,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
             cur = pi;
         }
         // ---- a1: the tile's columns of xi (or x_init, or the drawn samples) into rows 2..H+1
-        for (int e = tid; e < (HP + 2) * CP; e += NTHREADS) xs[e] = 0.0f;
+        for (int e = tid; e < (HP + 2) * CP; e += NTH) xs[e] = 0.0f;
         __syncthreads();
         if (p.s_mean) {
             // the samples covering the tile are contiguous in the batch: draw them by
@@ -1559,7 +1579,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
             const unsigned long long e0 = (unsigned long long)nf * HJ;
             const unsigned long long e1 = (unsigned long long)(nl_ + 1) * HJ;
             const unsigned long long q0b = e0 >> 2, q1b = (e1 + 3) >> 2;
-            for (unsigned long long q = q0b + tid; q < q1b; q += NTHREADS) {
+            for (unsigned long long q = q0b + tid; q < q1b; q += NTH) {
                 float z[4];
                 normals4(q, p.seed, p.sstream, z);
 #pragma unroll
@@ -1578,7 +1598,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
         } else {
             const float *src = p.x_init ? p.x_init : p.xi;
             const int total = Ct * H;
-            for (int e = tid; e < total; e += NTHREADS) {
+            for (int e = tid; e < total; e += NTH) {
                 const int k = e / Ct, cc = e - k * Ct;
                 const int col = C0 + cc, nn = col / J, j = col - nn * J;
                 xs[(k + 2) * CP + cc] = __ldg(src + ((size_t)nn * H + k) * J + j);
@@ -1664,7 +1684,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
             rowof(Mv, HQ) = rowof(Mp, HQ) = rowof(Ma, HQ) = rowof(Mj, HQ) = 0.0f;
         }
         __syncthreads();   // the slab is read: A (which it occupies) is cleared for the MMA
-        for (int e = tid; e < 128 * KD; e += NTHREADS) reinterpret_cast<float *>(As)[e] = 0.0f;
+        for (int e = tid; e < MROWS * KD; e += NTH) reinterpret_cast<float *>(As)[e] = 0.0f;
         __syncthreads();
         if (b == 0) {
             // K slot HQ of quarter 0: v0 of this column, split like the right-hand sides
@@ -1805,7 +1825,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
             }
             // ---- a5: K-apply, one M = 128 MMA per K-step (as in solve_kernel)
             if (warp == 0) {
-                const uint32_t idesc = umma_idesc_tf32(128, split ? 2 * ND : round_up(ND, 16));
+                const uint32_t idesc = umma_idesc_tf32(MROWS, split ? 2 * ND : round_up(ND, NW == 8 ? 16 : 8));
                 const uint32_t sbo = (uint32_t)(KD >> 2) * 128u;
                 const uint64_t da = umma_desc(smem_addr(As), 128u, sbo);
                 const uint64_t db = umma_desc(smem_addr(smem_raw + L.bhi), 128u, sbo);
@@ -1825,7 +1845,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
                 timed_out = true;   // X keeps the old iterate; the block stops at the next barrier
             } else {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t tl = tbase + ((uint32_t)(32 * (warp & 3) + 16 * (warp >> 2)) << 16);
+                const uint32_t tl = tbase + ((uint32_t)tl_lane << 16);
                 float xn[2 * NP];   // rows, then the sum of x over the earlier quarters
                 tmem_read_x<HQ + 1, ND>(tl, split, xn);
                 if (b == 0) xn[0] = colv ? v0j : 0.0f;   // x_0 = v0 exactly
@@ -1903,7 +1923,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
         __syncthreads();
         {
             const int total = Ct * H;
-            for (int e = tid; e < total; e += NTHREADS) {
+            for (int e = tid; e < total; e += NTH) {
                 const int k = e / Ct, cc = e - k * Ct;
                 const int col = C0 + cc, nn = col / J, j = col - nn * J;
                 p.out[((size_t)nn * H + k) * J + j] = xs[(k + 2) * CP + cc];
@@ -2138,15 +2158,17 @@ struct Variant {
     int hq;
     solve_fn admm, paper, admm_tc, paper_tc;       // one problem per launch
     solve_fn b_admm, b_paper, b_admm_tc, b_paper_tc;   // batched launches
+    solve_fn admm_tc4, b_admm_tc4;                 // ADMM on the tensor cores, 4-warp blocks (M = 64)
 };
 
 // The ADMM iteration with the tensor-core K-apply runs on solve_kernel_z; every
 // other combination on solve_kernel.
 #define VARIANT(HQv)                                                                                    \
     {HQv, solve_kernel<HQv, PRISM_MODE_ADMM, false, false>, solve_kernel<HQv, PRISM_MODE_PAPER, false, false>, \
-     solve_kernel_z<HQv, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false>,                            \
+     solve_kernel_z<HQv, 8, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false>,                         \
      solve_kernel<HQv, PRISM_MODE_ADMM, false, true>, solve_kernel<HQv, PRISM_MODE_PAPER, false, true>,       \
-     solve_kernel_z<HQv, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, true>}
+     solve_kernel_z<HQv, 8, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, true>,                           \
+     solve_kernel_z<HQv, 4, false>, solve_kernel_z<HQv, 4, true>}
 // prev_variant_hq (used for the rows that always exist) must list the same chunks.
 constexpr int kVariantHQ[] = {3, 5, 7, 9, 11, 13, 15, 17, 21, 25, 29, 33};
 constexpr bool variant_chain_ok()
@@ -2175,7 +2197,7 @@ bool tc_fits(int H)
     const Variant *v = pick_variant(H);
     if (!v) return false;
     const int n = H - 1;
-    return solve_smem(v->hq, n, (n + 3) & ~3, true).total <= 220 * 1024 && solve_smem_z(v->hq).total <= 220 * 1024 &&
+    return solve_smem(v->hq, n, (n + 3) & ~3, true).total <= 220 * 1024 && solve_smem_z(v->hq, 8).total <= 220 * 1024 &&
            2 * tc_nrows(v->hq) <= 256;
 }
 
@@ -2191,12 +2213,16 @@ prism_status check_handle(prism_proj_t h)
     return PRISM_OK;
 }
 
-int solve_ntiles(int batch, int J, bool flat)
+// Tiles of a batch: flat > 0 columns of the flattened [N][J] column index per
+// tile (solve_kernel_z), else whole samples, CMAX / J of them.
+int solve_ntiles(int batch, int J, int flat)
 {
-    if (flat) return (int)(((long long)batch * J + CMAX - 1) / CMAX);
+    if (flat > 0) return (int)(((long long)batch * J + flat - 1) / flat);
     const int T = std::max(1, CMAX / J);
     return (batch + T - 1) / T;
 }
+
+int z_warps(int hq);
 
 prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const float *v0,
                            const float *samples, int iters, double rho, float *out, SolveParams &p)
@@ -2218,8 +2244,9 @@ prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const flo
     p.T = std::max(1, CMAX / h->J);
     // the ADMM iteration with the tensor-core K-apply (solve_kernel_z) tiles the
     // flattened columns; the other kernels tile whole samples
-    p.flat = (h->mode == PRISM_MODE_ADMM && (h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32)) ? 1 : 0;
-    p.ntiles = solve_ntiles(batch, h->J, p.flat != 0);
+    p.flat = (h->mode == PRISM_MODE_ADMM && (h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32))
+                 ? 8 * z_warps(pick_variant(h->H)->hq) : 0;
+    p.ntiles = solve_ntiles(batch, h->J, p.flat);
     p.rho = (float)rho;
     p.dt = h->dt;
     p.wv = (float)w.wv; p.wa0 = (float)w.wa0; p.wa = (float)w.wa; p.wj0 = (float)w.wj0; p.wj = (float)w.wj;
@@ -2247,18 +2274,34 @@ LaunchParams single_launch(const SolveParams &p)
     return lp;
 }
 
-// Kernel function, dynamic shared memory and resident blocks per SM of one
-// solve-kernel variant.
-prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, int MP_max, int device,
-                            solve_fn &fn, size_t &smem, int &blocks_per_sm, int &hq)
+// Warps per block of solve_kernel_z by default: four (tiles of 32 columns, M =
+// 64 MMAs, twice the tensor-core time per column) where four such blocks fit on
+// an SM next to each other (shared and tensor memory), so that a block's MMA
+// wait is covered by three others; else eight (tiles of 64 columns, M = 128).
+int z_warps(int hq)
+{
+    const size_t smem = (size_t)solve_smem_z(hq, 4).total + 2048;   // + static shared memory and reserve
+    return (hq <= 17 && 4 * smem <= 228 * 1024 && 4 * tc_tmem_cols(hq) <= 512) ? 4 : 8;
+}
+
+// Kernel function, threads, dynamic shared memory and resident blocks per SM of
+// one solve-kernel variant.  nw: warps of solve_kernel_z (ADMM on the tensor
+// cores; 0 = z_warps), ignored by the other kernels.
+prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, int MP_max, int device, int nw,
+                            solve_fn &fn, int &threads, size_t &smem, int &blocks_per_sm, int &hq)
 {
     const Variant *v = pick_variant(H);
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", H);
     hq = v->hq;
-    if (!batched) fn = (mode == PRISM_MODE_ADMM) ? (tc ? v->admm_tc : v->admm) : (tc ? v->paper_tc : v->paper);
-    else fn = (mode == PRISM_MODE_ADMM) ? (tc ? v->b_admm_tc : v->b_admm) : (tc ? v->b_paper_tc : v->b_paper);
-    smem = (size_t)((tc && mode == PRISM_MODE_ADMM) ? solve_smem_z(v->hq).total
-                                                    : solve_smem(v->hq, n_max, MP_max, tc).total);
+    const bool z = tc && mode == PRISM_MODE_ADMM;
+    if (z && nw == 0) nw = z_warps(v->hq);
+    if (!z) nw = 8;
+    if (!batched) fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? v->admm_tc4 : v->admm_tc) : v->admm)
+                                               : (tc ? v->paper_tc : v->paper);
+    else fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? v->b_admm_tc4 : v->b_admm_tc) : v->b_admm)
+                                        : (tc ? v->b_paper_tc : v->b_paper);
+    threads = 32 * nw;
+    smem = (size_t)(z ? solve_smem_z(v->hq, nw).total : solve_smem(v->hq, n_max, MP_max, tc).total);
     // The dynamic shared-memory limit is a property of the kernel function, shared
     // by every handle and plan that launches it: only ever raise it.
     cudaFuncAttributes fa;
@@ -2267,14 +2310,14 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
         CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   (int)cudaSharedmemCarveoutMaxShared));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, (const void *)fn, NTHREADS, smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, (const void *)fn, threads, smem));
     int smem_sm = 0, reserved = 0, regs_sm = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
     CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
     CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, device));
     const size_t per_block = smem + fa.sharedSizeBytes + (size_t)reserved;
-    const int own = std::min(std::min((int)(smem_sm / per_block), regs_sm / std::max(1, fa.numRegs * NTHREADS)),
-                             2048 / NTHREADS);
+    const int own = std::min(std::min((int)(smem_sm / per_block), regs_sm / std::max(1, fa.numRegs * threads)),
+                             2048 / threads);
     blocks_per_sm = std::max(blocks_per_sm, own);
     // each resident block holds its accumulator in the SM's 512 tensor-memory columns
     if (tc) blocks_per_sm = std::min(blocks_per_sm, 512 / tc_tmem_cols(v->hq));
@@ -2283,19 +2326,20 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
 }
 
 prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t &smem, int &blocks_per_sm,
-                           int &grid, solve_fn &fn)
+                           int &grid, solve_fn &fn, int &threads)
 {
     v = pick_variant(h->H);
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", h->H);
     const bool tc = h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32;
     int hq;
-    prism_status st = variant_config(h->H, h->mode, tc, false, h->n, h->MP, h->device, fn, smem, blocks_per_sm, hq);
+    prism_status st = variant_config(h->H, h->mode, tc, false, h->n, h->MP, h->device, 0, fn, threads, smem,
+                                     blocks_per_sm, hq);
     if (st) return st;
-    const int ntiles = solve_ntiles(batch, h->J, tc && h->mode == PRISM_MODE_ADMM);
+    const bool z = tc && h->mode == PRISM_MODE_ADMM;
+    const int ntiles = solve_ntiles(batch, h->J, z ? threads / 4 : 0);
     grid = std::max(1, std::min(ntiles, blocks_per_sm * h->num_sms));
     return PRISM_OK;
 }
-
 
 // ===========================================================================
 // Batched plans: many independent problems (each with its own factored
@@ -2305,6 +2349,7 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
 struct PlanGroup {
     int hq = 0, mode = 0;
     bool tc = false;
+    int nw = 8, threads = NTHREADS;    // warps and threads per block of the group's kernel
     std::vector<int> members;          // indices into the plan's problem list
     std::vector<SolveParams> params;   // with tile0 prefix sums
     SolveParams *d_params = nullptr;   // device copy
@@ -2339,7 +2384,7 @@ namespace {
 prism_status plan_enqueue(prism_plan_t pl, cudaStream_t s)
 {
     for (PlanGroup &g : pl->groups) {
-        g.fn<<<g.grid, NTHREADS, g.smem, s>>>(g.lp);
+        g.fn<<<g.grid, g.threads, g.smem, s>>>(g.lp);
         CUDA_TRY(cudaGetLastError());
     }
     return PRISM_OK;
@@ -2377,7 +2422,7 @@ prism_status plan_time_group(prism_plan_t pl, PlanGroup &g, double &ms)
     ms = 1e30;
     for (int rep = 0; rep < 3; ++rep) {
         CUDA_TRY(cudaEventRecord(a, g.stream));
-        g.fn<<<grid, NTHREADS, g.smem, g.stream>>>(g.lp);
+        g.fn<<<grid, g.threads, g.smem, g.stream>>>(g.lp);
         CUDA_TRY(cudaGetLastError());
         CUDA_TRY(cudaEventRecord(b, g.stream));
         CUDA_TRY(cudaEventSynchronize(b));
@@ -2587,11 +2632,11 @@ prism_status prism_proj_solve(prism_proj_t h, int batch, const float *q0, const 
     p.dual = dual_res;
     const Variant *v;
     size_t smem;
-    int bps, grid;
+    int bps, grid, threads;
     solve_fn fn;
-    st = launch_config(h, batch, v, smem, bps, grid, fn);
+    st = launch_config(h, batch, v, smem, bps, grid, fn, threads);
     if (st) return st;
-    fn<<<grid, NTHREADS, smem, (cudaStream_t)cuda_stream>>>(single_launch(p));
+    fn<<<grid, threads, smem, (cudaStream_t)cuda_stream>>>(single_launch(p));
     CUDA_TRY(cudaGetLastError());
     return PRISM_OK;
 }
@@ -2617,11 +2662,11 @@ prism_status prism_proj_solve_ex(prism_proj_t h, int batch, const float *q0, con
     p.dual = dual_res;
     const Variant *v;
     size_t smem;
-    int bps, grid;
+    int bps, grid, threads;
     solve_fn fn;
-    st = launch_config(h, batch, v, smem, bps, grid, fn);
+    st = launch_config(h, batch, v, smem, bps, grid, fn, threads);
     if (st) return st;
-    fn<<<grid, NTHREADS, smem, (cudaStream_t)cuda_stream>>>(single_launch(p));
+    fn<<<grid, threads, smem, (cudaStream_t)cuda_stream>>>(single_launch(p));
     CUDA_TRY(cudaGetLastError());
     return PRISM_OK;
 }
@@ -2647,11 +2692,11 @@ prism_status prism_proj_sample_solve(prism_proj_t h, int batch, const float *q0,
     p.dual = dual_res;
     const Variant *v;
     size_t smem;
-    int bps, grid;
+    int bps, grid, threads;
     solve_fn fn;
-    st = launch_config(h, batch, v, smem, bps, grid, fn);
+    st = launch_config(h, batch, v, smem, bps, grid, fn, threads);
     if (st) return st;
-    fn<<<grid, NTHREADS, smem, (cudaStream_t)cuda_stream>>>(single_launch(p));
+    fn<<<grid, threads, smem, (cudaStream_t)cuda_stream>>>(single_launch(p));
     CUDA_TRY(cudaGetLastError());
     return PRISM_OK;
 }
@@ -2859,15 +2904,15 @@ prism_status prism_proj_query(prism_proj_t h, int batch, long long out[8])
     if (!h->factored) return fail(PRISM_ERR_NOT_FACTORED, "prism_proj_factor has not been called");
     const Variant *v;
     size_t smem;
-    int bps, grid;
+    int bps, grid, threads;
     solve_fn fn;
-    st = launch_config(h, std::max(batch, 1), v, smem, bps, grid, fn);
+    st = launch_config(h, std::max(batch, 1), v, smem, bps, grid, fn, threads);
     if (st) return st;
     cudaFuncAttributes attr;
     CUDA_TRY(cudaFuncGetAttributes(&attr, (const void *)fn));
     const int T = std::max(1, CMAX / h->J);
     const bool flat = h->mode == PRISM_MODE_ADMM && (h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32);
-    out[0] = flat ? CMAX : (long long)T * h->J;
+    out[0] = flat ? threads / 4 : (long long)T * h->J;
     out[1] = flat ? 0 : T;   // 0: tiles of flattened columns (not whole samples)
     out[2] = bps;
     out[3] = grid;
@@ -2946,7 +2991,8 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             g.lp.n_max = n_max;
             g.lp.MP_max = MP_max;
             int hq;
-            st = variant_config(Hmax, g.mode, g.tc, true, n_max, MP_max, dev, g.fn, g.smem, g.bps, hq);
+            st = variant_config(Hmax, g.mode, g.tc, true, n_max, MP_max, dev, 0, g.fn, g.threads, g.smem, g.bps, hq);
+            g.nw = g.threads / 32;
             if (st) break;
             if (!g.params.empty()) {
                 cudaError_t e = dev_malloc(&g.d_params, sizeof(SolveParams) * g.params.size());
@@ -2988,20 +3034,33 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             double ms = 0.0;
             st = plan_time_group(pl, g, ms);
             if (st) break;
+            // alternatives: the other K-apply path (when every problem of the group is
+            // FP32-accurate on both) and, on the tensor-core ADMM kernel, the other
+            // tile width (32 columns / four warps or 64 / eight)
             bool can_switch = true;
             for (int k : g.members) {
                 const int prec = probs[k].h->prec;
                 if (prec == PRISM_PREC_TF32 || (!g.tc && !tc_fits(probs[k].h->H))) can_switch = false;
             }
-            if (can_switch) {
-                // the other kernel tiles the columns differently: its own descriptor table
+            int Hmax = 2;
+            for (int k : g.members) Hmax = std::max(Hmax, probs[k].h->H);
+            std::vector<std::pair<bool, int>> cands;
+            if (can_switch) cands.push_back({!g.tc, 0});
+            if (g.tc && g.mode == PRISM_MODE_ADMM) cands.push_back({true, g.nw == 4 ? 8 : 4});
+            for (const auto &cd : cands) {
                 PlanGroup alt = g;
-                alt.tc = !g.tc;
+                alt.tc = cd.first;
                 alt.d_params = nullptr;
-                const bool flat = alt.tc && alt.mode == PRISM_MODE_ADMM;
+                int hq;
+                st = variant_config(Hmax, alt.mode, alt.tc, true, alt.lp.n_max, alt.lp.MP_max, dev, cd.second, alt.fn,
+                                    alt.threads, alt.smem, alt.bps, hq);
+                if (st) break;
+                alt.nw = alt.threads / 32;
+                // the kernel's tiling: its own descriptor table
+                const int flat = (alt.tc && alt.mode == PRISM_MODE_ADMM) ? 8 * alt.nw : 0;
                 int tiles = 0;
                 for (SolveParams &sp : alt.params) {
-                    sp.flat = flat ? 1 : 0;
+                    sp.flat = flat;
                     sp.ntiles = solve_ntiles(sp.N, sp.J, flat);
                     sp.tile0 = tiles;
                     tiles += sp.ntiles;
@@ -3019,26 +3078,22 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
                     break;
                 }
                 alt.lp.many = alt.d_params;
-                int hq;
-                int Hmax = 2;
-                for (int k : g.members) Hmax = std::max(Hmax, probs[k].h->H);
-                st = variant_config(Hmax, alt.mode, alt.tc, true, alt.lp.n_max, alt.lp.MP_max, dev, alt.fn, alt.smem,
-                                    alt.bps, hq);
                 double ms2 = 0.0;
-                if (!st) st = plan_time_group(pl, alt, ms2);
+                st = plan_time_group(pl, alt, ms2);
                 if (st) {
                     cudaFree(alt.d_params);
                     break;
                 }
                 if (ms2 < ms) {
                     cudaFree(g.d_params);
-                    g.tc = alt.tc; g.fn = alt.fn; g.smem = alt.smem; g.bps = alt.bps; g.lp = alt.lp;
-                    g.params = alt.params; g.d_params = alt.d_params;
+                    g.tc = alt.tc; g.nw = alt.nw; g.threads = alt.threads; g.fn = alt.fn; g.smem = alt.smem;
+                    g.bps = alt.bps; g.lp = alt.lp; g.params = alt.params; g.d_params = alt.d_params;
                     ms = ms2;
                 } else {
                     cudaFree(alt.d_params);
                 }
             }
+            if (st) break;
             g.tuned_ms = ms;
         }
         if (!st) {
