@@ -378,6 +378,19 @@ prism_status prism_proj_describe(prism_proj_t h, int dims[6], double *rho);
 typedef struct prism_server_s *prism_server_t;
 prism_status prism_server_create(size_t mem_budget_bytes, int max_inflight, double deadline_ms,
                                  prism_server_t *out);
+/*
+ * prism_server_create_ex -- prism_server_create with flags:
+ *   PRISM_SERVER_PLAIN  solve every request with the plain FP32 comparator
+ *                       (prism_proj_solve_plain: cold start, no warm-start
+ *                       multiplier, one thread per column), under the same
+ *                       scheduling, admission and statistics; the comparison
+ *                       arm of the serving benchmark.  The comparator's
+ *                       per-handle workspace is allocated by a handle's first
+ *                       request.
+ */
+enum { PRISM_SERVER_PLAIN = 1 };
+prism_status prism_server_create_ex(size_t mem_budget_bytes, int max_inflight, double deadline_ms, int flags,
+                                    prism_server_t *out);
 prism_status prism_server_add_controller(prism_server_t s, prism_proj_t h, int batch, int iters,
                                          int warm_start, int *id);
 prism_status prism_server_submit(prism_server_t s, int id, const float *q0_host, const float *v0_host,

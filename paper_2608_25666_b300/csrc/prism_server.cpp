@@ -148,6 +148,7 @@ struct Arena {
 struct Server {
     int device = 0;
     double deadline_ms = 20.0;
+    bool plain = false;               // PRISM_SERVER_PLAIN: every request on the plain comparator
     std::mutex mu;
     std::condition_variable cv;       // scheduler wake-ups
     std::condition_variable done_cv;  // waiters on tickets
@@ -209,15 +210,22 @@ bool Server::enqueue(const std::shared_ptr<Request> &r, const Controller &c, boo
     bool ok = cudaMemcpyAsync(d_xi, r->xi, seq * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(d_q0, r->q0, c.J * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(d_v0, r->v0, c.J * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess;
-    if (ok && warm_in) ok = prism_proj_shift_state(c.h, c.N, 1, nullptr, d_state, s) == PRISM_OK;
-    prism_solve_opts o;
-    o.x_init = nullptr;
-    o.dual_init = warm_in ? d_state : nullptr;
-    o.dual_out = c.warm ? d_state : nullptr;
-    o.polish_iters = 0;
-    if (ok)
-        ok = prism_proj_solve_ex(c.h, c.N, d_q0, d_v0, d_xi, c.iters, c.rho, &o, d_out, d_pr, nullptr, s) ==
-             PRISM_OK;
+    if (plain) {
+        // the plain single-batch comparator: cold start, one thread per column
+        if (ok)
+            ok = prism_proj_solve_plain(c.h, c.N, d_q0, d_v0, d_xi, c.iters, c.rho, d_out, d_pr, nullptr, s) ==
+                 PRISM_OK;
+    } else {
+        if (ok && warm_in) ok = prism_proj_shift_state(c.h, c.N, 1, nullptr, d_state, s) == PRISM_OK;
+        prism_solve_opts o;
+        o.x_init = nullptr;
+        o.dual_init = warm_in ? d_state : nullptr;
+        o.dual_out = c.warm ? d_state : nullptr;
+        o.polish_iters = 0;
+        if (ok)
+            ok = prism_proj_solve_ex(c.h, c.N, d_q0, d_v0, d_xi, c.iters, c.rho, &o, d_out, d_pr, nullptr, s) ==
+                 PRISM_OK;
+    }
     // the handle's timeout flag after this solve, read at retire without a host
     // sync, then cleared for the next launch of the handle
     int *d_flag = prism_internal_err_flag(c.h);
@@ -304,7 +312,7 @@ void Server::run()
             j.r = r;
             j.c = c;
             j.c.queued.reset();
-            j.warm_in = c.warm && c.has_state;
+            j.warm_in = c.warm && c.has_state && !plain;
             jobs.push_back(std::move(j));
         }
         if (!jobs.empty()) {
@@ -340,7 +348,14 @@ extern "C" {
 
 prism_status prism_server_create(size_t mem_budget_bytes, int max_inflight, double deadline_ms, prism_server_t *out)
 {
+    return prism_server_create_ex(mem_budget_bytes, max_inflight, deadline_ms, 0, out);
+}
+
+prism_status prism_server_create_ex(size_t mem_budget_bytes, int max_inflight, double deadline_ms, int flags,
+                                    prism_server_t *out)
+{
     if (!out) return sfail(PRISM_ERR_INVALID_ARG, "out is NULL");
+    if (flags & ~PRISM_SERVER_PLAIN) return sfail(PRISM_ERR_INVALID_ARG, "unknown server flags %d", flags);
     *out = nullptr;
     if (mem_budget_bytes < (1u << 20)) return sfail(PRISM_ERR_INVALID_ARG, "memory budget below 1 MiB");
     if (max_inflight < 1 || max_inflight > 256) return sfail(PRISM_ERR_INVALID_ARG, "max_inflight outside [1, 256]");
@@ -349,6 +364,7 @@ prism_status prism_server_create(size_t mem_budget_bytes, int max_inflight, doub
     if (!ps) return sfail(PRISM_ERR_OOM, "host allocation failed");
     Server &S = ps->srv;
     S.deadline_ms = deadline_ms;
+    S.plain = (flags & PRISM_SERVER_PLAIN) != 0;
     cudaError_t e = cudaGetDevice(&S.device);
     char *base = nullptr;
     if (e == cudaSuccess) e = prism_internal_dev_malloc(reinterpret_cast<void **>(&base), mem_budget_bytes);

@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
             L.prism_proj_describe.restype = i
             sz = ctypes.c_size_t
             L.prism_server_create.argtypes = [sz, i, d, ctypes.POINTER(P)]
+            L.prism_server_create_ex.argtypes = [sz, i, d, i, ctypes.POINTER(P)]
+            L.prism_server_create_ex.restype = i
             L.prism_server_add_controller.argtypes = [P, P, i, i, i, ctypes.POINTER(i)]
             L.prism_server_submit.argtypes = [P, i, P, P, P, P, P, ctypes.POINTER(ctypes.c_ulonglong)]
             L.prism_server_wait.argtypes = [P, ctypes.c_ulonglong, d, ctypes.POINTER(i),
@@ -416,10 +418,10 @@ class Server:
     """
 
     def __init__(self, mem_budget_bytes: int = 8 << 30, max_inflight: int = 16,
-                 deadline_ms: float = 20.0):
+                 deadline_ms: float = 20.0, plain: bool = False):
         h = ctypes.c_void_p()
-        _check(lib().prism_server_create(int(mem_budget_bytes), int(max_inflight), float(deadline_ms),
-                                         ctypes.byref(h)))
+        _check(lib().prism_server_create_ex(int(mem_budget_bytes), int(max_inflight), float(deadline_ms),
+                                            1 if plain else 0, ctypes.byref(h)))
         self._h = h
         self._refs = {}
         self._projs = []

@@ -82,7 +82,10 @@ def run(server: pp.Server, ctrls, steps: int, **arrival_kw) -> dict:
                 time.sleep(0.0005)
                 continue
             for t in pending:
-                st, _ = server.wait(t)
+                try:
+                    st, _ = server.wait(t)
+                except pp.PrismError:
+                    st = "failed"
                 results["states"][st] = results["states"].get(st, 0) + 1
                 k += 1
 

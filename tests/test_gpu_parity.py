@@ -327,21 +327,36 @@ def test_warm_start_and_multiplier_export(prec, mode):
 
 
 def test_tf32_single_pass_with_polish():
-    """Single-pass TF32 K-apply plus FP32-accurate polish: the error against the
-    oracle is measured and reported; with all iterations split it meets the bar."""
+    """Precision workload shape (J=14, H=64, 120 iterations): single-pass TF32
+    K-apply followed by split (FP32-accurate) polish iterations.  Measured on the
+    full precision workload: no polish count short of all 120 meets the bar
+    (100 polish iterations still leave max |dx| = 1.8e-3: the early single-pass
+    iterations move the iterate off the FP64 trajectory and the remaining ones
+    do not bring it back).  The gated configuration is therefore the smallest
+    one that meets it, polish = iterations, which is the split K-apply; both
+    spellings of it are checked on every column against the oracle."""
     import torch
-    b = workloads.make_custom(91, 40, 14, 64, 0.02)
-    P = pp.Projector(14, 64, 0.02, b["bounds"]).factor(1.0, prec=pp.PREC_TF32)
+    b = workloads.make_custom(91, 256, 14, 64, 0.02)
     xi, q0, v0 = to_dev(b)
     o = oracle_solve(b, 120, 1.0)
     errs = {}
-    for polish in (0, 20, 120):
+    P = pp.Projector(14, 64, 0.02, b["bounds"]).factor(1.0, prec=pp.PREC_TF32)
+    for polish in (0, 20, 100, 120):
         x, pr, du, _ = P.solve_ex(q0, v0, xi, 120, polish_iters=polish)
         torch.cuda.synchronize()
-        errs[polish] = float(np.max(np.abs(x.cpu().numpy() - o["x"])))
-    print("TF32 single pass + polish, max|dx| by polish count:", errs)
-    assert errs[120] <= X_TOL
+        g = {"x": x.cpu().numpy().astype(np.float64), "primal": pr.cpu().numpy().astype(np.float64),
+             "dual": du.cpu().numpy().astype(np.float64)}
+        errs[polish] = (float(np.max(np.abs(g["x"] - o["x"]))), float(np.max(np.abs(g["primal"] - o["primal"]))))
+        if polish == 120:
+            assert_parity(g, o)
     P.close()
+    print("TF32 single pass + polish, (max|dx|, max|dviol|) by polish count:", errs)
+    Q = pp.Projector(14, 64, 0.02, b["bounds"]).factor(1.0, prec=pp.PREC_TF32X3)
+    x, pr, du = Q.solve(q0, v0, xi, 120)
+    torch.cuda.synchronize()
+    assert_parity({"x": x.cpu().numpy().astype(np.float64), "primal": pr.cpu().numpy().astype(np.float64),
+                   "dual": du.cpu().numpy().astype(np.float64)}, o)
+    Q.close()
 
 
 @pytest.mark.parametrize("mode", [pp.MODE_ADMM, pp.MODE_PAPER])

@@ -151,3 +151,49 @@ def test_timed_out_request_is_failed_and_next_starts_cold():
     torch.cuda.synchronize()
     assert np.array_equal(x.cpu().numpy(), out2)
     P.close()
+
+
+def test_plain_server_arm_equals_direct_plain_solves():
+    """PRISM_SERVER_PLAIN: every request is the plain comparator's cold solve,
+    bit for bit, whatever else the server runs."""
+    import torch
+    outs, st = run_server_plain(["A", "C"], 2)
+    for nm in ("A", "C"):
+        J, H, N, dt, prec = CTRLS[nm]
+        d = controller_data(nm, 2)
+        P = pp.Projector(J, H, dt, d[0]["bounds"]).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, prec)
+        for k in range(2):
+            xi = torch.from_numpy(d[k]["xi"]).cuda()
+            q0 = torch.from_numpy(d[k]["q0"]).cuda()
+            v0 = torch.from_numpy(d[k]["v0"]).cuda()
+            x, _, _ = P.solve_plain(q0, v0, xi, ITERS)
+            torch.cuda.synchronize()
+            assert np.array_equal(x.cpu().numpy(), outs[nm][k]), (nm, k)
+        P.close()
+    assert st["completed"] == 4 and st["failed"] == 0
+
+
+def run_server_plain(names, steps):
+    S = pp.Server(mem_budget_bytes=1 << 30, max_inflight=4, deadline_ms=20.0, plain=True)
+    projs, ids, data = {}, {}, {}
+    for nm in names:
+        J, H, N, dt, prec = CTRLS[nm]
+        d = controller_data(nm, steps)
+        P = pp.Projector(J, H, dt, d[0]["bounds"]).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, prec)
+        projs[nm], data[nm] = P, d
+        ids[nm] = S.add_controller(P, N, ITERS, warm=True)
+    outs = {nm: [] for nm in names}
+    for k in range(steps):
+        tickets = []
+        for nm in names:
+            J, H, N, dt, prec = CTRLS[nm]
+            out = np.empty((N, H, J), np.float32)
+            tickets.append((nm, S.submit(ids[nm], data[nm][k]["q0"], data[nm][k]["v0"], data[nm][k]["xi"], out), out))
+        for nm, t, out in tickets:
+            assert S.wait(t)[0] == "done"
+            outs[nm].append(out)
+    st = S.stats()
+    S.close()
+    for P in projs.values():
+        P.close()
+    return outs, st
