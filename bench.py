@@ -38,6 +38,10 @@ PRECS = {"fp32": 0, "tf32x3": 3}
 # from one ncu capture of that launch, keyed by the hash of the kernel source's code (comments and whitespace
 # removed) it was taken on: a changed kernel reports null until it is captured
 # again.
+# ncu pipe utilisation of the same launch (sm__pipe_*_cycles_active and issue
+# activity, % of peak sustained), keyed like MEASURED_TRAFFIC.
+MEASURED_PIPES = {}
+
 MEASURED_TRAFFIC = {
     "fp32": {"kernel_source_sha256_16": "a1725e577f0a6b70", "bytes": 9912576},
     "tf32x3": {"kernel_source_sha256_16": "5f5358680ac5c901", "bytes": 9950208},
@@ -68,6 +72,19 @@ def measured_traffic(prec: str):
     return rec["bytes"]
 
 
+def measured_pipes(prec: str):
+    rec = MEASURED_PIPES.get(prec)
+    if not rec or rec["kernel_source_sha256_16"] != kernel_source_hash():
+        return None
+    return {k: v for k, v in rec.items() if k != "kernel_source_sha256_16"}
+
+
+def kapply_flops_per_column_iteration(H: int) -> int:
+    """Algorithmic flops of the K-apply (x_2..x_H = K' rhs + kb' v0) of one column
+    and iteration: the part that runs on the tensor cores."""
+    return 2 * (H - 1) ** 2 + 2 * (H - 1)
+
+
 def flops_per_column_iteration(H: int) -> int:
     """Algorithmic FP32 flops of one iteration of one column (ADMM mode).
 
@@ -80,6 +97,27 @@ def flops_per_column_iteration(H: int) -> int:
       K-apply on x_2..x_H           2 (H-1)^2 + 2 (H-1)   (kb v0 term)
     """
     return 2 * (H - 1) ** 2 + 43 * H - 19
+
+
+def pipe_rooflines(flops_total: float, flops_kapply: float, seconds: float, num_sms: int, peaks: dict,
+                   counters=None) -> dict:
+    """Per-pipe roofline of one launch: the stencil, clip and multiplier work
+    (everything but the K-apply) against the FP32 issue rate, the K-apply against
+    the tf32 tensor rate (half the measured bf16 rate).  counters: ncu pipe
+    utilisations of the same kernel, or None."""
+    simt = flops_total - flops_kapply
+    p_simt = peak_fp32_tflops(num_sms, 2032.0)
+    bf16 = peaks.get("bf16_tflops")
+    p_tc = 0.5 * bf16 if bf16 else None
+    out = {"simt": {"achieved": simt / seconds / 1e12, "peak": p_simt, "unit": "TFLOP/s",
+                    "frac": simt / seconds / 1e12 / p_simt,
+                    "peak_basis": "FP32 FMA issue rate, 2032 MHz (derived)"},
+           "tensor": {"achieved": flops_kapply / seconds / 1e12, "peak": p_tc, "unit": "TFLOP/s",
+                      "frac": (flops_kapply / seconds / 1e12 / p_tc) if p_tc else None,
+                      "peak_basis": "tf32 dense = 0.5 x measured bf16 burst (%s TFLOP/s, of measured)" % bf16}}
+    if counters:
+        out["ncu"] = counters
+    return out
 
 
 def peak_fp32_tflops(num_sms: int, mhz: float) -> float:
@@ -512,6 +550,8 @@ def config_dict():
 
 
 def main():
+    import faulthandler
+    faulthandler.enable()   # a crash prints the Python stacks of every thread
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1280)
@@ -699,6 +739,9 @@ def main():
                               " (max SM clock; derived, no measured FP32 peak)",
                 "algorithmic_flops_per_launch": flops,
                 "algorithmic_bytes_per_launch": 2 * w.N * w.H * w.J * 4 + 2 * w.N * w.J * 4}
+    kflops = w.N * w.J * w.iters * kapply_flops_per_column_iteration(w.H) if args.prec != "fp32" else 0
+    roofline_pipes = pipe_rooflines(flops, kflops, avg_launch_s, q["num_sms"], load_peaks(),
+                                    measured_pipes(args.prec))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -732,6 +775,7 @@ def main():
                                          "each call; consecutive independent steps overlap"},
                 "gpu_launches": K,
                 "roofline": roofline,
+                "roofline_pipes": roofline_pipes,
                 "clocks": clocks,
                 "launch": q,
                 "wall_s_timed": t_wall}

@@ -373,7 +373,8 @@ prism_status prism_proj_describe(prism_proj_t h, int dims[6], double *rho);
  *   (late or dropped), out[7] completed trajectories, out[8] trajectories/s
  *   between the first submission and the last completion, out[9] free arena
  *   bytes.  prism_server_reset_stats clears them.
- * prism_server_destroy: finish in-flight work, stop the scheduler, free the arena.
+ * prism_server_destroy: stop the scheduler (queued requests that have not started
+ *   are abandoned), finish the work in flight and its completions, free the arena.
  */
 typedef struct prism_server_s *prism_server_t;
 prism_status prism_server_create(size_t mem_budget_bytes, int max_inflight, double deadline_ms,

@@ -183,11 +183,15 @@ namespace {
 void CUDART_CB on_request_done(void *arg)
 {
     // runs on the CUDA callback thread: no CUDA calls and no locks here; the
-    // scheduler polls at least every 200 microseconds
+    // scheduler polls at least every 200 microseconds.  Once the state is
+    // stored the scheduler may retire the request and its waiter free it, so
+    // nothing of the request is touched after the store (the server outlives
+    // every callback: destroy synchronises the streams first).
     Request *r = static_cast<Request *>(arg);
+    Server *srv = r->srv;
     r->t_done = now_s();
     r->state.store(Q_DONE);
-    r->srv->cv.notify_all();
+    srv->cv.notify_all();
 }
 
 }  // namespace
@@ -537,14 +541,15 @@ prism_status prism_server_destroy(prism_server_t ps)
 {
     if (!ps) return sfail(PRISM_ERR_INVALID_ARG, "null server");
     Server &S = ps->srv;
-    // let in-flight work finish, then stop the scheduler
-    for (cudaStream_t s : S.streams) cudaStreamSynchronize(s);
+    // stop the scheduler (no new work is enqueued after it returns), then let the
+    // work in flight and its completion callbacks finish
     {
         std::lock_guard<std::mutex> lk(S.mu);
         S.stop = true;
     }
     S.cv.notify_all();
     if (S.th.joinable()) S.th.join();
+    for (cudaStream_t s : S.streams) cudaStreamSynchronize(s);
     for (cudaStream_t s : S.streams) cudaStreamDestroy(s);
     cudaFreeHost(S.slot_flag);
     cudaFree(S.arena.base);

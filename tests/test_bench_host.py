@@ -34,3 +34,17 @@ def test_code_hash_ignores_comments_and_layout_only():
     assert b.code_hash(src) == b.code_hash("int f(int a) { return a + 1; }")
     assert b.code_hash(src) != b.code_hash("int f(int a) { return a + 2; }")
     assert len(b.kernel_source_hash()) == 16
+
+
+def test_pipe_rooflines_split_the_work_between_the_pipes():
+    b = _bench()
+    H = 50
+    total = b.flops_per_column_iteration(H)
+    kap = b.kapply_flops_per_column_iteration(H)
+    assert kap == 2 * 49 ** 2 + 2 * 49 and 0 < kap < total
+    r = b.pipe_rooflines(total * 1e9, kap * 1e9, 1.0, 148, {"bf16_tflops": 1800.0})
+    assert abs(r["simt"]["achieved"] - (total - kap) * 1e-3) < 1e-9
+    assert abs(r["tensor"]["peak"] - 900.0) < 1e-9
+    assert abs(r["tensor"]["frac"] - kap * 1e-3 / 900.0) < 1e-12
+    assert "ncu" not in r
+    assert b.pipe_rooflines(1.0, 0.0, 1.0, 148, {})["tensor"]["frac"] is None
