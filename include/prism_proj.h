@@ -252,6 +252,17 @@ prism_status prism_proj_get_factor(prism_proj_t h, double *K_host, double *kb_ho
 prism_status prism_proj_query(prism_proj_t h, int batch, long long out[8]);
 
 /*
+ * prism_proj_set_tiling -- tile shape of this handle's ADMM solves on the tensor
+ * cores (PRISM_MODE_ADMM with PRISM_PREC_TF32X3 or PRISM_PREC_TF32; other
+ * handles ignore it).  warps: 0 the library's default; 4 or 8 tiles of 32 or 64
+ * columns, four threads per column; 16 tiles of 64 columns with eight threads
+ * per column (eight time quarters, every cross-quarter term carried by the
+ * MMA; 52 < H <= 104, else PRISM_ERR_UNSUPPORTED).  Results are those of the
+ * same iteration up to FP32 rounding order.  Plans choose their own tiling.
+ */
+prism_status prism_proj_set_tiling(prism_proj_t h, int warps);
+
+/*
  * prism_proj_solve_plain_noalloc -- prism_proj_solve_plain for callers that
  * must not allocate device memory when they solve.
  *

@@ -170,7 +170,9 @@ struct prism_proj_s {
     float *d_kb32 = nullptr;             // [MP]
     float *d_wp = nullptr;               // [PRISM_MAX_H] position-row weights
     float *d_Khi = nullptr, *d_Klo = nullptr;   // [n+4][n+4] tf32 split of [K' | kb' | C] + quarter-prefix rows
+    float *d_Khi8 = nullptr, *d_Klo8 = nullptr; // [n+8][n+22] eight-quarter operand (52 < H <= 104, tensor cores)
     int *d_err = nullptr;                // tensor-core wait timeout flag
+    int tiling = 0;                      // prism_proj_set_tiling: 0 default, 4 / 8 / 16 warps
     double *d_wfull = nullptr;           // factor input: per-row weights (4 blocks x H)
     // plain comparator workspace
     float *d_work = nullptr;
@@ -196,7 +198,8 @@ __device__ __forceinline__ double d2c(int m, int i)
 __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wrow,
                               double *__restrict__ K64, double *__restrict__ kb64,
                               float *__restrict__ Kt32, float *__restrict__ kb32, int MP,
-                              float *__restrict__ Khi32, float *__restrict__ Klo32, int hq)
+                              float *__restrict__ Khi32, float *__restrict__ Klo32, int hq,
+                              float *__restrict__ Khi8, float *__restrict__ Klo8, int hq8)
 {
     extern __shared__ double Bs[];   // H*H
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -306,6 +309,59 @@ __global__ void factor_kernel(int H, double rho_c, const double *__restrict__ wr
         Khi32[(n + bq) * KW + j] = hi;
         Klo32[(n + bq) * KW + j] = (float)(acc - (double)hi);
     }
+    if (!Khi8) return;
+    // Operand of the eight-quarter kernel (quarters of hq8 steps), row stride
+    // KW8 = n + 22: [K' | kb' | C | S | T] with, for each quarter start b = 1..7,
+    //   C_b = sum of K' columns over the unknowns before quarter b (position
+    //         totals of the later quarters, the L^T suffix sum across quarters),
+    //   T_b = K' column of time L = b*hq8 - 1, the last step before quarter b
+    //         (the next quarter's first acceleration term q_0 of F^T, which the
+    //         first difference toward the future hands to time L),
+    //   S_b = K' column of time L minus that of time L - 1 (the next quarter's
+    //         first jerk term sj_0, which the two first differences hand to
+    //         times L (+) and L - 1 (-)),
+    // and eight rows n + b: the sum of x over the time steps before quarter b,
+    // x_0 = v0 included.
+    __syncthreads();
+    double *C8 = Bs + 3 * n;   // [n][7]
+    for (int i = tid; i < n; i += nth) {
+        double run = 0.0;
+        int cc = 0;
+        for (int bq = 1; bq <= 7; ++bq) {
+            const int cend = min(bq * hq8, H) - 2;
+            for (; cc <= cend; ++cc) run += K64[i * n + cc];
+            C8[i * 7 + bq - 1] = run;
+        }
+    }
+    __syncthreads();
+    const int KW8 = n + 22;
+    const auto col8 = [&](int i, int j) -> double {
+        if (j < n) return K64[i * n + j];
+        if (j == n) return kb64[i];
+        const int q = j - n - 1, kind = q / 7, bq = q - kind * 7 + 1;
+        if (kind == 0) return C8[i * 7 + bq - 1];
+        const int Lr = bq * hq8 - 2;   // unknown index of time L
+        const double t = (Lr >= 0 && Lr < n) ? K64[i * n + Lr] : 0.0;
+        if (kind == 2) return t;
+        return t - ((Lr - 1 >= 0 && Lr - 1 < n) ? K64[i * n + Lr - 1] : 0.0);
+    };
+    for (int e = tid; e < (n + 8) * KW8; e += nth) {
+        const int i = e / KW8, j = e - i * KW8;
+        double v;
+        if (i < n) {
+            v = col8(i, j);
+        } else {
+            const int bq = i - n, iend = min(bq * hq8 - 1, n);
+            v = (j == n && bq >= 1) ? 1.0 : 0.0;
+            for (int t = 1; t <= iend; ++t) v += col8(t - 1, j);
+        }
+        uint32_t r;
+        const float kf = (float)v;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(kf));
+        const float hi = __uint_as_float(r);
+        Khi8[e] = hi;
+        Klo8[e] = (float)(v - (double)hi);
+    }
 }
 
 // ===========================================================================
@@ -326,6 +382,8 @@ struct SolveParams {
     const float *__restrict__ wp;        // [>= H]
     const float *__restrict__ Khi;       // [n+4][n+4] tf32 high part of [K' | kb' | C] and the quarter-prefix rows
     const float *__restrict__ Klo;       // [n+4][n+4] remainder - Khi
+    const float *__restrict__ Khi8;      // [n+8][n+22] tf32 high part of the eight-quarter operand (or NULL)
+    const float *__restrict__ Klo8;      // its remainder
     int *err;                            // set to 1 if a tensor-core wait ran out
     const float *x_init;                 // [N][H][J] warm-start iterate or NULL (x^0 = xi)
     const float *dual_init;              // [N][D][J] warm-start multiplier or NULL (0)
@@ -589,6 +647,11 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
 }
 
+// Programmatic dependent launch: the grid launched after this one on the stream
+// with programmatic serialisation may start once every block of this one has
+// executed this (or exited).  No-op without a dependent launch.
+__device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // One lane of the (converged) warp.
 __device__ __forceinline__ bool elect_one()
 {
@@ -835,6 +898,9 @@ solve_kernel(const __grid_constant__ LaunchParams P)
     int cur = -1;
 
     for (int tile = blockIdx.x; tile < P.ntiles && !aborted; tile += gridDim.x) {
+        // a block on its last tile lets a dependent launch start (plans chain their
+        // groups that way: the next group fills the SMs this one leaves)
+        if (tile + (int)gridDim.x >= P.ntiles) launch_dependents();
         // problem of this tile (block-uniform): binary search over first tiles
         int pi = 0;
         if (BATCHED) {
@@ -1512,6 +1578,9 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
     const float2 TWO = make_float2(2.0f, 2.0f);
 
     for (int tile = blockIdx.x; tile < P.ntiles && !aborted; tile += gridDim.x) {
+        // a block on its last tile lets a dependent launch start (plans chain their
+        // groups that way: the next group fills the SMs this one leaves)
+        if (tile + (int)gridDim.x >= P.ntiles) launch_dependents();
         int pi = 0;
         if (BATCHED) {
             int lo = 0, hi = P.nprob - 1;
@@ -1940,6 +2009,529 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
 }
 
 // ===========================================================================
+// K3 for the longer horizons: eight-quarter tiles.  The iteration of
+// solve_kernel_z with eight threads per column (each owning HQ time steps,
+// H <= 8 HQ), 64 columns per 512-thread block, M = 128.  Warp w owns columns
+// 16 (w % 4) + 8 (w / 8 % 2) + lane / 4, quarter 4 (w / 4 % 2) + lane % 4: the
+// two halves of a column's quarters sit in warps w and w + 4 of the same
+// tensor-memory lane quarter, so both read the column's accumulator rows.
+// Nothing crosses quarters inside the iteration except through the MMA:
+//   - D holds, per quarter, its HQ steps, the sum of x over the earlier
+//     quarters and the two steps before it (the stencil halo);
+//   - quarter b >= 1 writes into its three spare K slots -rho times its
+//     position total, rho times its first jerk term sj_0 and rho times its
+//     first acceleration term q_0; the operand's columns C, S, T carry them
+//     to the earlier time steps (the L^T suffix sum and the first
+//     differences of F^T that cross the quarter start).
+// 128 registers a thread (16 warps a block, one block per SM) where the
+// four-quarter kernel would need up to 255 for the same horizon.
+// ===========================================================================
+struct Q8Smem {
+    int a, bhi, xi, wt, red, total;
+};
+
+__host__ __device__ constexpr int q8_nq(int hq) { return 4 * (hq + 3); }   // D columns of one quarter half
+
+__host__ __device__ inline Q8Smem solve_smem_q8(int hq)
+{
+    const int KD = 8 * tc_hq4(hq), NQ = q8_nq(hq), NP = (hq + 1) / 2;
+    Q8Smem L;
+    int off = 0;
+    L.a = off;   off += 128 * KD * 4;               // A operand; the tile slab outside the iteration
+    L.bhi = off; off += 4 * NQ * KD * 4;            // B: two quarter halves, high parts over low parts
+    L.xi = off;  off += 512 * z_xi_stride(hq) * 4;  // xi, each thread's rows contiguous
+    L.wt = off;  off += 3 * 8 * NP * 8;             // weight pairs: position, acceleration, jerk x quarter x pair
+    L.red = off; off += 64 * 8 * 4;                 // per column and quarter: prologue sums, epilogue maxima
+    L.total = off;
+    return L;
+}
+
+template <int HQ, bool BATCHED>
+__global__ void __launch_bounds__(512, 1)
+solve_kernel_q8(const __grid_constant__ LaunchParams P)
+{
+    constexpr int NTH = 512, CM = 64, QN = 8;
+    constexpr int HP = QN * HQ;
+    constexpr int CP = CM + 8;
+    constexpr int HQ4 = tc_hq4(HQ), KD = QN * HQ4, NQ = q8_nq(HQ);
+    constexpr int NP = (HQ + 1) / 2;
+    constexpr int TMEM_COLS = 256;
+    static_assert(HQ & 1, "row pairs assume an odd horizon chunk (one spare row)");
+    static_assert(HQ4 - HQ == 3, "three spare K slots per quarter");
+    static_assert(4 * NQ <= 256, "N of one MMA");
+    static_assert(3 * NQ + 16 * ((HQ + 3 + 3) / 4) <= TMEM_COLS, "the readback reads past the allocation");
+    static_assert((HP + 2) * CP <= 128 * KD, "the tile slab must fit in the A operand");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mma_bar;
+    const Q8Smem L = solve_smem_q8(HQ);
+    unsigned char *As = smem_raw + L.a;
+    float *xs = reinterpret_cast<float *>(smem_raw + L.a);
+    const float2 *wtab = reinterpret_cast<const float2 *>(smem_raw + L.wt);
+    float *red = reinterpret_cast<float *>(smem_raw + L.red);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int sp = warp & 3, hh = (warp >> 3) & 1, qh = (warp >> 2) & 1;
+    const int c = 16 * sp + 8 * hh + (lane >> 2);   // column in tile
+    const int bl = lane & 3;
+    const int b = 4 * qh + bl;                       // quarter
+    const int i0 = b * HQ;
+    constexpr int SX = z_xi_stride(HQ);
+    float *xit = reinterpret_cast<float *>(smem_raw + L.xi) + tid * SX;
+    const float2 *xit2 = reinterpret_cast<const float2 *>(xit);
+    const int arow_hi = 32 * sp + 16 * hh + (lane >> 2);
+    const int tl_lane = 32 * sp + 16 * hh;
+    float *ahi = reinterpret_cast<float *>(As + cm_off(arow_hi, HQ4 * b, KD));
+    constexpr int LO = 8 * KD;
+    float *aw[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) aw[m] = ahi + (m ^ bl);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tmem_slot)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mma_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = tmem_slot;
+    uint32_t mma_phase = 0;
+    bool aborted = false, timed_out = false;
+    int cur = -1;
+    const float2 TWO = make_float2(2.0f, 2.0f);
+
+    for (int tile = blockIdx.x; tile < P.ntiles && !aborted; tile += gridDim.x) {
+        // a block on its last tile lets a dependent launch start (plans chain their
+        // groups that way: the next group fills the SMs this one leaves)
+        if (tile + (int)gridDim.x >= P.ntiles) launch_dependents();
+        int pi = 0;
+        if (BATCHED) {
+            int lo = 0, hi = P.nprob - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (P.many[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+            }
+            pi = lo;
+        }
+        const SolveParams &p = BATCHED ? P.many[pi] : P.one;
+        const int H = p.H, J = p.J, n = p.n;
+        const int HJ = H * J;
+        const float rho = p.rho;
+        const int iters = p.iters, polish = p.polish;
+        const int C0 = (tile - p.tile0) * CM;
+        const int Ct = min(CM, p.N * J - C0);
+        __syncthreads();   // previous tile fully stored before the slab is overwritten
+        if (pi != cur) {
+            // per-problem operand B (rows: D columns of both quarter halves, high
+            // parts over low parts; K: right-hand-side slots, v0 and the quarter
+            // terms in the spare slots) and the weight pairs
+            const int KW8 = n + 22;
+            for (int e = tid; e < 4 * NQ * KD; e += NTH) {
+                const int pr = e / KD, kq = e - pr * KD;
+                const bool low = pr >= 2 * NQ;
+                const int pc = low ? pr - 2 * NQ : pr;
+                const int qhh = pc / NQ, pcl = pc - qhh * NQ;
+                const int k = pcl >> 2, bq = 4 * qhh + (pcl & 3);
+                int i;   // row of the operand, -1 zero, -2 the x_0 = v0 row
+                if (k < HQ) {
+                    const int xt = bq * HQ + k;
+                    i = (xt >= 1 && xt <= n) ? xt - 1 : -1;
+                } else if (k == HQ) {
+                    i = n + bq;
+                } else {
+                    const int xt = bq * HQ - 2 + (k - HQ - 1);
+                    i = (xt >= 1 && xt <= n) ? xt - 1 : (xt == 0 ? -2 : -1);
+                }
+                const int kb_ = kq / HQ4, kr = kq - kb_ * HQ4;
+                const int rr = (kr & ~3) | ((kr & 3) ^ (kb_ & 3));
+                const int xk = kb_ * HQ + rr;
+                int j = -1;
+                if (rr < HQ) j = (xk >= 1 && xk <= n) ? xk - 1 : -1;
+                else if (rr == HQ) j = (kb_ == 0) ? n : n + kb_;
+                else if (kb_ >= 1) j = (rr == HQ + 1) ? n + 7 + kb_ : n + 14 + kb_;
+                float v = 0.0f;
+                if (i >= 0 && j >= 0) v = low ? p.Klo8[i * KW8 + j] : p.Khi8[i * KW8 + j];
+                else if (i == -2 && j == n && !low) v = 1.0f;
+                *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, kq, KD)) = v;
+            }
+            float *wt = reinterpret_cast<float *>(smem_raw + L.wt);
+            for (int e = tid; e < 3 * 16 * NP; e += NTH) {
+                const int kind = e / (16 * NP), rem = e - kind * 16 * NP;
+                const int bq = rem / (2 * NP), r = rem - bq * 2 * NP;
+                const int i = bq * HQ + r;
+                const bool ex = r < HQ && i < H;
+                float w = 0.0f;
+                if (kind == 0) w = ex ? p.wp[i] : 0.0f;
+                else if (kind == 1) w = ex ? (i == 0 ? p.wa0 : p.wa) : 0.0f;
+                else w = (ex && i >= 1) ? (i == 1 ? p.wj0 : p.wj) : 0.0f;
+                wt[e] = w;
+            }
+            cur = pi;
+        }
+        // ---- a1: the tile's columns of xi (or x_init, or the drawn samples) into rows 2..H+1
+        for (int e = tid; e < (HP + 2) * CP; e += NTH) xs[e] = 0.0f;
+        __syncthreads();
+        if (p.s_mean) {
+            const int nf = C0 / J, nl_ = (C0 + Ct - 1) / J;
+            const unsigned long long e0 = (unsigned long long)nf * HJ;
+            const unsigned long long e1 = (unsigned long long)(nl_ + 1) * HJ;
+            const unsigned long long q0b = e0 >> 2, q1b = (e1 + 3) >> 2;
+            for (unsigned long long q = q0b + tid; q < q1b; q += NTH) {
+                float z[4];
+                normals4(q, p.seed, p.sstream, z);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned long long e = 4 * q + u;
+                    if (e < e0 || e >= e1) continue;
+                    const int nn = (int)(e / HJ), rem = (int)(e - (unsigned long long)nn * HJ);
+                    const int k = rem / J, j = rem - k * J;
+                    const int cc = nn * J + j - C0;
+                    if (cc < 0 || cc >= Ct) continue;
+                    const float v = fmaf(p.s_std[rem], z[u], p.s_mean[rem]);
+                    xs[(k + 2) * CP + cc] = v;
+                    if (p.xi_out) p.xi_out[e] = v;
+                }
+            }
+        } else {
+            const float *src = p.x_init ? p.x_init : p.xi;
+            const int total = Ct * H;
+            for (int e = tid; e < total; e += NTH) {
+                const int k = e / Ct, cc = e - k * Ct;
+                const int col = C0 + cc, nn = col / J, j = col - nn * J;
+                xs[(k + 2) * CP + cc] = __ldg(src + ((size_t)nn * H + k) * J + j);
+            }
+        }
+        __syncthreads();
+        // ---- a2: bounds, x^0 (x_0 := v0), the halo and the sum over earlier quarters
+        const bool colv = c < Ct;
+        const int n_c = colv ? (C0 + c) / J : 0;
+        const int jj = colv ? (C0 + c) - n_c * J : 0;
+        const float q0j = p.q0[jj], v0j = p.v0[jj];
+        const ColBounds cb = col_bounds(p.bounds, J, jj, p.dt, q0j, v0j);
+        const float alo_r0 = (b == 0) ? cb.alo0 : cb.alo, ahi_r0 = (b == 0) ? cb.ahi0 : cb.ahi;
+        const float jlo_r1 = (b == 0) ? cb.jlo1 : cb.jlo, jhi_r1 = (b == 0) ? cb.jhi1 : cb.jhi;
+        float2 X[NP];
+        float h0, h1;
+        {
+            float run = 0.0f;
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) {
+                rowof(X, r) = (r == 0 && b == 0) ? (colv ? v0j : 0.0f) : xs[(i0 + r + 2) * CP + c];
+                run += rowof(X, r);
+            }
+            h0 = xs[i0 * CP + c];
+            h1 = (b == 0) ? 0.0f : xs[(i0 + 1) * CP + c];
+            red[c * 8 + b] = run;
+        }
+        {
+            const float *xisrc = p.xi + (size_t)n_c * HJ + jj;
+#pragma unroll
+            for (int r = 0; r < 2 * NP; ++r) {
+                float v = 0.0f;
+                if (r < HQ && colv && i0 + r < H) v = p.x_init ? __ldg(xisrc + (size_t)(i0 + r) * J) : xs[(i0 + r + 2) * CP + c];
+                xit[r] = v;
+            }
+        }
+        __syncthreads();
+        {
+            float pre = 0.0f;
+            for (int bq = 0; bq < b; ++bq) pre += red[c * 8 + bq];
+            rowof(X, HQ) = pre;
+        }
+        const auto rows_y = [&](float2 (&Yp)[NP], float2 (&Ya)[NP], float2 (&Yj)[NP]) {
+            float cs = rowof(X, HQ), xm1 = h1, am1 = h1 - h0;
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) {
+                const float xr = rowof(X, r);
+                cs += xr;
+                const float ya = xr - xm1;
+                rowof(Yp, r) = cs;
+                rowof(Ya, r) = ya;
+                rowof(Yj, r) = ya - am1;
+                xm1 = xr;
+                am1 = ya;
+            }
+            rowof(Yp, HQ) = 0.0f;
+            rowof(Ya, HQ) = 0.0f;
+            rowof(Yj, HQ) = 0.0f;
+        };
+        const size_t dbase = (size_t)n_c * p.D * J + jj;
+        const auto u0 = [&](int kind, int i) -> float {
+            if (!p.dual_init || !colv || i >= H) return 0.0f;
+            if (kind == 0) return __ldg(p.dual_init + dbase + (size_t)i * J) * rsqrtf(p.wv);
+            if (kind == 1) return __ldg(p.dual_init + dbase + (size_t)(H + i) * J) * rsqrtf(p.wp[i]);
+            if (kind == 2) return __ldg(p.dual_init + dbase + (size_t)(2 * H + i) * J) * rsqrtf(i == 0 ? p.wa0 : p.wa);
+            if (i < 1) return 0.0f;
+            return __ldg(p.dual_init + dbase + (size_t)(3 * H + i - 1) * J) * rsqrtf(i == 1 ? p.wj0 : p.wj);
+        };
+        float2 Mv[NP], Mp[NP], Ma[NP], Mj[NP];
+        {
+            float2 Yp[NP], Ya[NP], Yj[NP];
+            rows_y(Yp, Ya, Yj);
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) {
+                const int i = i0 + r;
+                const bool vi = colv && i < H;
+                rowof(Mv, r) = vi ? u0(0, i) - rowof(X, r) : 0.0f;
+                rowof(Mp, r) = vi ? u0(1, i) - rowof(Yp, r) : 0.0f;
+                rowof(Ma, r) = vi ? u0(2, i) - rowof(Ya, r) : 0.0f;
+                rowof(Mj, r) = (vi && i >= 1) ? u0(3, i) - rowof(Yj, r) : 0.0f;
+            }
+            rowof(Mv, HQ) = rowof(Mp, HQ) = rowof(Ma, HQ) = rowof(Mj, HQ) = 0.0f;
+        }
+        __syncthreads();   // the slab and the sums are read: A is cleared for the MMA
+        for (int e = tid; e < 128 * KD; e += NTH) reinterpret_cast<float *>(As)[e] = 0.0f;
+        __syncthreads();
+        if (b == 0) {
+            const float v = colv ? v0j : 0.0f;
+            const float hi = tf32_rna(v);
+            aw[HQ & 3][32 * (HQ >> 2)] = hi;
+            aw[HQ & 3][32 * (HQ >> 2) + LO] = v - hi;
+        }
+        float dmax = 0.0f;
+
+        for (int l = 0; l < iters; ++l) {
+            // ---- a3, a6, a4 as in solve_kernel_z, quarter-local: the next quarter's
+            // first sj and q reach this quarter's last rows through the MMA
+            float2 G[NP];
+            float T, sj0, q0;
+            {
+                {
+                    float2 Zp[NP];
+                    float cs = rowof(X, HQ);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        cs += X[k].x;
+                        const float c0 = cs;
+                        if (2 * k + 1 < HQ) cs += X[k].y;
+                        const float2 y = make_float2(c0, (2 * k + 1 < HQ) ? cs : 0.0f);
+                        const float2 w = fma2(TWO, y, Mp[k]);
+                        Zp[k] = clamp2(w, cb.plo, cb.phi, cb.plo, cb.phi);
+                        Mp[k] = sub2(sub2(w, y), Zp[k]);
+                    }
+                    float Pc = 0.0f, Podd = 0.0f;
+#pragma unroll
+                    for (int r = HQ - 1; r >= 0; --r) {
+                        const float2 wp2 = wtab[b * NP + (r >> 1)];
+                        Pc = fmaf((r & 1) ? wp2.y : wp2.x, rowof(Mp, r), Pc);
+                        if (r & 1) Podd = Pc;
+                        else G[r >> 1] = make_float2(Pc, (r + 1 < HQ) ? Podd : 0.0f);
+                    }
+                    T = Pc;
+                }
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    const float2 w = fma2(TWO, X[k], Mv[k]);
+                    const float2 z = clamp2(w, cb.vlo, cb.vhi, cb.vlo, cb.vhi);
+                    Mv[k] = sub2(sub2(w, X[k]), z);
+                    G[k] = add2(G[k], Mv[k]);
+                }
+                float2 D[NP];
+                {
+                    float xm1 = h1, am1 = h1 - h0;
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        const float a0 = X[k].x - xm1;
+                        const float j0 = a0 - am1;
+                        const float a1 = X[k].y - X[k].x;
+                        const float j1 = a1 - a0;
+                        xm1 = X[k].y;
+                        am1 = a1;
+                        const float2 y = make_float2(j0, (2 * k + 1 < HQ) ? j1 : 0.0f);
+                        const float2 w = fma2(TWO, y, Mj[k]);
+                        const float2 z = (k == 0) ? clamp2(w, cb.jlo, cb.jhi, jlo_r1, jhi_r1)
+                                                  : clamp2(w, cb.jlo, cb.jhi, cb.jlo, cb.jhi);
+                        Mj[k] = sub2(sub2(w, y), z);
+                        D[k] = mul2(wtab[(16 + b) * NP + k], Mj[k]);
+                    }
+                    sj0 = D[0].x;
+#pragma unroll
+                    for (int r = 0; r < HQ; ++r) rowof(D, r) = rowof(D, r) - ((r + 1 < HQ) ? rowof(D, r + 1) : 0.0f);
+                }
+                {
+                    float xm1 = h1;
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        const float a0 = X[k].x - xm1;
+                        const float a1 = X[k].y - X[k].x;
+                        xm1 = X[k].y;
+                        const float2 y = make_float2(a0, (2 * k + 1 < HQ) ? a1 : 0.0f);
+                        const float2 w = fma2(TWO, y, Ma[k]);
+                        const float2 z = (k == 0) ? clamp2(w, alo_r0, ahi_r0, cb.alo, cb.ahi)
+                                                  : clamp2(w, cb.alo, cb.ahi, cb.alo, cb.ahi);
+                        Ma[k] = sub2(sub2(w, y), z);
+                        D[k] = fma2(wtab[(8 + b) * NP + k], Ma[k], D[k]);
+                    }
+                    q0 = D[0].x;
+#pragma unroll
+                    for (int r = 0; r < HQ; ++r) rowof(D, r) = rowof(D, r) - ((r + 1 < HQ) ? rowof(D, r + 1) : 0.0f);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) G[k] = add2(G[k], D[k]);
+                }
+            }
+            const bool last = (l == iters - 1);
+            const bool split = l >= iters - polish;
+            float2 RV[NP];
+            {
+                const float2 NRHO2 = make_float2(-rho, -rho);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) RV[k] = fma2(NRHO2, G[k], xit2[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const int r = 2 * k;
+                const float2 hi2 = make_float2(tf32_round(RV[k].x), (r + 1 < HQ) ? tf32_round(RV[k].y) : 0.0f);
+                const float2 lo2 = sub2(RV[k], hi2);
+                aw[r & 3][32 * (r >> 2)] = hi2.x;
+                if (split) aw[r & 3][32 * (r >> 2) + LO] = lo2.x;
+                if (r + 1 < HQ) {
+                    aw[(r + 1) & 3][32 * ((r + 1) >> 2)] = hi2.y;
+                    if (split) aw[(r + 1) & 3][32 * ((r + 1) >> 2) + LO] = lo2.y;
+                }
+            }
+            if (b > 0) {
+                // this quarter's terms for the earlier time steps: -rho * position total,
+                // rho * first jerk term, rho * first acceleration term
+                const float t0 = -rho * T, t1 = rho * sj0, t2 = rho * q0;
+                const float e0 = tf32_round(t0), e1 = tf32_round(t1), e2 = tf32_round(t2);
+                aw[HQ & 3][32 * (HQ >> 2)] = e0;
+                aw[(HQ + 1) & 3][32 * ((HQ + 1) >> 2)] = e1;
+                aw[(HQ + 2) & 3][32 * ((HQ + 2) >> 2)] = e2;
+                if (split) {
+                    aw[HQ & 3][32 * (HQ >> 2) + LO] = t0 - e0;
+                    aw[(HQ + 1) & 3][32 * ((HQ + 1) >> 2) + LO] = t1 - e1;
+                    aw[(HQ + 2) & 3][32 * ((HQ + 2) >> 2) + LO] = t2 - e2;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (__syncthreads_or(timed_out)) {
+                aborted = true;
+                break;
+            }
+            // ---- a5: K-apply, one M = 128 MMA per K-step over both quarter halves
+            if (warp == 0) {
+                const uint32_t idesc = umma_idesc_tf32(128, split ? 4 * NQ : round_up(2 * NQ, 16));
+                const uint32_t sbo = (uint32_t)(KD >> 2) * 128u;
+                const uint64_t da = umma_desc(smem_addr(As), 128u, sbo);
+                const uint64_t db = umma_desc(smem_addr(smem_raw + L.bhi), 128u, sbo);
+                if (elect_one()) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    for (int ks = 0; ks < (KD >> 3); ++ks) {
+                        const uint64_t kk = (uint64_t)(16 * ks);
+                        umma_tf32(tbase, da + kk, db + kk, idesc, ks > 0 ? 1u : 0u);
+                    }
+                    umma_commit(smem_addr(&mma_bar));
+                }
+                __syncwarp();
+            }
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mma_bar), mma_phase));
+            mma_phase ^= 1u;
+            if (!ok) {
+                timed_out = true;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tl = tbase + ((uint32_t)tl_lane << 16) + (uint32_t)(qh * NQ);
+                float xn[HQ + 3];   // rows, the sum over earlier quarters, the two halo steps
+                tmem_read_x<HQ + 3, 2 * NQ>(tl, split, xn);
+                if (b == 0) xn[0] = colv ? v0j : 0.0f;
+                if (last) {
+#pragma unroll
+                    for (int r = 0; r < HQ; ++r) {
+                        const int i = i0 + r;
+                        if (i >= 1 && i < H) dmax = fmaxf(dmax, fabsf(xn[r] - rowof(X, r)));
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < NP; ++k) X[k] = make_float2(xn[2 * k], xn[2 * k + 1]);
+                h0 = xn[HQ + 1];
+                h1 = xn[HQ + 2];
+            }
+        }
+        if (__syncthreads_or(aborted || timed_out)) {
+            if (tid == 0 && p.err) atomicExch(p.err, 1);
+            aborted = true;
+        }
+        if (aborted) break;
+
+        // ---- a7: residuals, final multiplier, store
+        float2 Yp[NP], Ya[NP], Yj[NP];
+        rows_y(Yp, Ya, Yj);
+        float viol = 0.0f;
+#pragma unroll
+        for (int r = 0; r < HQ; ++r) {
+            const int i = i0 + r;
+            if (i < H) {
+                const float yv = rowof(X, r), yp = rowof(Yp, r), ya = rowof(Ya, r), yj = rowof(Yj, r);
+                viol = fmaxf(viol, fmaxf(yv - cb.vhi, cb.vlo - yv));
+                viol = fmaxf(viol, fmaxf(yp - cb.phi, cb.plo - yp) * inv_norm_pos(i));
+                const float ea = (i == 0) ? fmaxf(ya - cb.ahi0, cb.alo0 - ya)
+                                          : fmaxf(ya - cb.ahi, cb.alo - ya) * 0.70710678f;
+                viol = fmaxf(viol, ea);
+                if (i >= 1) {
+                    const float ej = (i == 1) ? fmaxf(yj - cb.jhi1, cb.jlo1 - yj) * 0.44721360f
+                                              : fmaxf(yj - cb.jhi, cb.jlo - yj) * 0.40824829f;
+                    viol = fmaxf(viol, ej);
+                }
+            }
+        }
+        if (p.dual_out && colv) {
+            const size_t base = (size_t)n_c * p.D * J + jj;
+#pragma unroll
+            for (int r = 0; r < HQ; ++r) {
+                const int i = i0 + r;
+                if (i < H) {
+                    p.dual_out[base + (size_t)i * J] = sqrtf(p.wv) * (rowof(Mv, r) + rowof(X, r));
+                    p.dual_out[base + (size_t)(H + i) * J] = sqrtf(p.wp[i]) * (rowof(Mp, r) + rowof(Yp, r));
+                    p.dual_out[base + (size_t)(2 * H + i) * J] =
+                        sqrtf(i == 0 ? p.wa0 : p.wa) * (rowof(Ma, r) + rowof(Ya, r));
+                    if (i >= 1)
+                        p.dual_out[base + (size_t)(3 * H + i - 1) * J] =
+                            sqrtf(i == 1 ? p.wj0 : p.wj) * (rowof(Mj, r) + rowof(Yj, r));
+                }
+            }
+        }
+        // maxima over the column's eight quarters: four in the warp, then the two warps
+        viol = fmaxf(viol, __shfl_xor_sync(0xffffffffu, viol, 1, 4));
+        viol = fmaxf(viol, __shfl_xor_sync(0xffffffffu, viol, 2, 4));
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, 1, 4));
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, 2, 4));
+        if (bl == 0) {
+            red[c * 8 + qh] = viol;
+            red[c * 8 + 2 + qh] = dmax;
+        }
+        // the final iterate back to the slab (in A, whose last MMA has completed)
+#pragma unroll
+        for (int r = 0; r < HQ; ++r) xs[(i0 + r + 2) * CP + c] = rowof(X, r);
+        __syncthreads();
+        if (b == 0 && colv) {
+            const size_t col = (size_t)C0 + c;
+            if (p.primal) p.primal[col] = fmaxf(red[c * 8], red[c * 8 + 1]);
+            if (p.dual) p.dual[col] = fmaxf(red[c * 8 + 2], red[c * 8 + 3]);
+        }
+        {
+            const int total = Ct * H;
+            for (int e = tid; e < total; e += NTH) {
+                const int k = e / Ct, cc = e - k * Ct;
+                const int col = C0 + cc, nn = col / J, j = col - nn * J;
+                p.out[((size_t)nn * H + k) * J + j] = xs[(k + 2) * CP + cc];
+            }
+        }
+    }
+    if (aborted && tid == 0) (void)mbar_wait(smem_addr(&mma_bar), mma_phase ^ 1u);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(TMEM_COLS));
+}
+
+// ===========================================================================
 // K2: plain FP32 comparator.  One thread per column; the iterate, the
 // multiplier rows and the right-hand side live in a workspace laid out
 // [row][column] (coalesced across threads); K is read through the L1 cache.
@@ -2224,6 +2816,21 @@ int solve_ntiles(int batch, int J, int flat)
 
 int z_warps(int hq);
 
+// Eight-quarter tiles (solve_kernel_q8): quarters of 9 (H <= 72) or 13 steps
+// (H <= 104), for the ADMM iteration on the tensor cores with 52 < H <= 104.
+// Measured slower than the four-quarter kernels on single solves at most
+// horizons (the one block per SM waits out its larger MMA), so they are never
+// the default: prism_proj_set_tiling selects them, and plans try them.
+int q8_hq(int H) { return H <= 72 ? 9 : (H <= 104 ? 13 : 0); }
+bool q8_capable(int H) { return H > 52 && q8_hq(H) > 0; }
+
+// Warps per block of the ADMM tensor-core kernel for a handle: its tiling
+// choice, else the default (four or eight warps, four-quarter tiles).
+int handle_warps(const prism_proj_s *h)
+{
+    return h->tiling ? h->tiling : z_warps(pick_variant(h->H)->hq);
+}
+
 prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const float *v0,
                            const float *samples, int iters, double rho, float *out, SolveParams &p)
 {
@@ -2244,8 +2851,12 @@ prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const flo
     p.T = std::max(1, CMAX / h->J);
     // the ADMM iteration with the tensor-core K-apply (solve_kernel_z) tiles the
     // flattened columns; the other kernels tile whole samples
-    p.flat = (h->mode == PRISM_MODE_ADMM && (h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32))
-                 ? 8 * z_warps(pick_variant(h->H)->hq) : 0;
+    if (h->mode == PRISM_MODE_ADMM && (h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32)) {
+        const int nw = handle_warps(h);
+        p.flat = nw == 16 ? 64 : 8 * nw;
+    } else {
+        p.flat = 0;
+    }
     p.ntiles = solve_ntiles(batch, h->J, p.flat);
     p.rho = (float)rho;
     p.dt = h->dt;
@@ -2253,6 +2864,7 @@ prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const flo
     p.xi = samples; p.q0 = q0; p.v0 = v0; p.bounds = h->d_bounds;
     p.Kt = h->d_Kt32; p.kb = h->d_kb32; p.wp = h->d_wp;
     p.Khi = h->d_Khi; p.Klo = h->d_Klo; p.err = h->d_err;
+    p.Khi8 = h->d_Khi8; p.Klo8 = h->d_Klo8;
     p.x_init = nullptr; p.dual_init = nullptr; p.dual_out = nullptr;
     p.D = (h->mode == PRISM_MODE_ADMM) ? 4 * h->H - 1 : h->H;
     p.tile0 = 0;
@@ -2296,12 +2908,23 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
     const bool z = tc && mode == PRISM_MODE_ADMM;
     if (z && nw == 0) nw = z_warps(v->hq);
     if (!z) nw = 8;
-    if (!batched) fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? v->admm_tc4 : v->admm_tc) : v->admm)
-                                               : (tc ? v->paper_tc : v->paper);
-    else fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? v->b_admm_tc4 : v->b_admm_tc) : v->b_admm)
-                                        : (tc ? v->b_paper_tc : v->b_paper);
+    if (nw == 16) {
+        // eight-quarter tiles: 512 threads, one block per SM
+        const int hq8 = q8_hq(H);
+        if (!z || hq8 == 0) return fail(PRISM_ERR_UNSUPPORTED, "eight-quarter tiles need ADMM on the tensor cores, H <= 104");
+        hq = hq8;
+        fn = (hq8 == 9) ? (batched ? solve_kernel_q8<9, true> : solve_kernel_q8<9, false>)
+                        : (batched ? solve_kernel_q8<13, true> : solve_kernel_q8<13, false>);
+        smem = (size_t)solve_smem_q8(hq8).total;
+    } else if (!batched) {
+        fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? v->admm_tc4 : v->admm_tc) : v->admm)
+                                       : (tc ? v->paper_tc : v->paper);
+    } else {
+        fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? v->b_admm_tc4 : v->b_admm_tc) : v->b_admm)
+                                       : (tc ? v->b_paper_tc : v->b_paper);
+    }
     threads = 32 * nw;
-    smem = (size_t)(z ? solve_smem_z(v->hq, nw).total : solve_smem(v->hq, n_max, MP_max, tc).total);
+    if (nw != 16) smem = (size_t)(z ? solve_smem_z(v->hq, nw).total : solve_smem(v->hq, n_max, MP_max, tc).total);
     // The dynamic shared-memory limit is a property of the kernel function, shared
     // by every handle and plan that launches it: only ever raise it.
     cudaFuncAttributes fa;
@@ -2320,7 +2943,7 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
                              2048 / threads);
     blocks_per_sm = std::max(blocks_per_sm, own);
     // each resident block holds its accumulator in the SM's 512 tensor-memory columns
-    if (tc) blocks_per_sm = std::min(blocks_per_sm, 512 / tc_tmem_cols(v->hq));
+    if (tc) blocks_per_sm = std::min(blocks_per_sm, nw == 16 ? 2 : 512 / tc_tmem_cols(v->hq));
     if (blocks_per_sm < 1) return fail(PRISM_ERR_UNSUPPORTED, "solve kernel does not fit on an SM (smem %zu)", smem);
     return PRISM_OK;
 }
@@ -2332,11 +2955,12 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", h->H);
     const bool tc = h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32;
     int hq;
-    prism_status st = variant_config(h->H, h->mode, tc, false, h->n, h->MP, h->device, 0, fn, threads, smem,
+    const int nw = (tc && h->mode == PRISM_MODE_ADMM) ? handle_warps(h) : 0;
+    prism_status st = variant_config(h->H, h->mode, tc, false, h->n, h->MP, h->device, nw, fn, threads, smem,
                                      blocks_per_sm, hq);
     if (st) return st;
     const bool z = tc && h->mode == PRISM_MODE_ADMM;
-    const int ntiles = solve_ntiles(batch, h->J, z ? threads / 4 : 0);
+    const int ntiles = solve_ntiles(batch, h->J, z ? (threads == 512 ? 64 : threads / 4) : 0);
     grid = std::max(1, std::min(ntiles, blocks_per_sm * h->num_sms));
     return PRISM_OK;
 }
@@ -2383,9 +3007,24 @@ namespace {
 // partially filled SMs of the others.)
 prism_status plan_enqueue(prism_plan_t pl, cudaStream_t s)
 {
+    // groups after the first are programmatic dependents of the one before: the
+    // problems are independent, so a group's blocks may start as soon as the
+    // previous group's blocks are on their last tiles (its tail overlaps the
+    // next group's start; nothing waits on the previous group's results)
+    bool first = true;
     for (PlanGroup &g : pl->groups) {
-        g.fn<<<g.grid, g.threads, g.smem, s>>>(g.lp);
-        CUDA_TRY(cudaGetLastError());
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)g.grid);
+        cfg.blockDim = dim3((unsigned)g.threads);
+        cfg.dynamicSmemBytes = g.smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = first ? 0 : 1;
+        CUDA_TRY(cudaLaunchKernelEx(&cfg, g.fn, g.lp));
+        first = false;
     }
     return PRISM_OK;
 }
@@ -2580,14 +3219,20 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
         if (e == cudaSuccess) e = dev_malloc(&Klo, sizeof(float) * (n + 4) * (n + 4));
         if (e == cudaSuccess) e = dev_malloc(&err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+        float *Khi8 = nullptr, *Klo8 = nullptr;
+        if (e == cudaSuccess && q8_capable(H)) {
+            e = dev_malloc(&Khi8, sizeof(float) * (n + 8) * (n + 22));
+            if (e == cudaSuccess) e = dev_malloc(&Klo8, sizeof(float) * (n + 8) * (n + 22));
+        }
         if (e != cudaSuccess) {
             cudaFree(K64); cudaFree(kb64); cudaFree(Kt32); cudaFree(kb32); cudaFree(wp);
-            cudaFree(wfull); cudaFree(Khi); cudaFree(Klo); cudaFree(err);
+            cudaFree(wfull); cudaFree(Khi); cudaFree(Klo); cudaFree(err); cudaFree(Khi8); cudaFree(Klo8);
             return fail(e == cudaErrorMemoryAllocation ? PRISM_ERR_OOM : PRISM_ERR_CUDA, "factor buffers: %s",
                         cudaGetErrorString(e));
         }
         h->d_K64 = K64; h->d_kb64 = kb64; h->d_Kt32 = Kt32; h->d_kb32 = kb32; h->d_wp = wp;
         h->d_wfull = wfull; h->d_Khi = Khi; h->d_Klo = Klo; h->d_err = err;
+        h->d_Khi8 = Khi8; h->d_Klo8 = Klo8;
     }
     const Weights w = make_weights(scale, h->dt);
     double wfull[4 * PRISM_MAX_H];
@@ -2608,7 +3253,7 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
     const Variant *fv = pick_variant(H);
     if (!fv) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", H);
     factor_kernel<<<1, 256, smem, s>>>(H, rho_c, h->d_wfull, h->d_K64, h->d_kb64, h->d_Kt32, h->d_kb32, MP,
-                                       h->d_Khi, h->d_Klo, fv->hq);
+                                       h->d_Khi, h->d_Klo, fv->hq, h->d_Khi8, h->d_Klo8, q8_hq(H));
     CUDA_TRY(cudaGetLastError());
     // the host tables above are stack memory: make sure the copies completed
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -2912,13 +3557,13 @@ prism_status prism_proj_query(prism_proj_t h, int batch, long long out[8])
     CUDA_TRY(cudaFuncGetAttributes(&attr, (const void *)fn));
     const int T = std::max(1, CMAX / h->J);
     const bool flat = h->mode == PRISM_MODE_ADMM && (h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32);
-    out[0] = flat ? threads / 4 : (long long)T * h->J;
+    out[0] = flat ? (threads == 512 ? 64 : threads / 4) : (long long)T * h->J;
     out[1] = flat ? 0 : T;   // 0: tiles of flattened columns (not whole samples)
     out[2] = bps;
     out[3] = grid;
     out[4] = (long long)smem;
     out[5] = attr.numRegs;
-    out[6] = v->hq;
+    out[6] = (threads == 512) ? q8_hq(h->H) : v->hq;
     out[7] = h->num_sms;
     return PRISM_OK;
 }
@@ -2937,7 +3582,7 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
     pl->iters = iters;
     pl->flags = flags;
     prism_status st = PRISM_OK;
-    std::map<std::tuple<int, int, int>, int> index;   // (hq, mode, tc) -> group
+    std::map<std::tuple<int, int, int>, int> index;   // (kernel class, mode, tc) -> group
     std::vector<SolveParams> all(nprob);
     std::vector<bool> use_tc(nprob);
     for (int k = 0; k < nprob && !st; ++k) {
@@ -2993,6 +3638,19 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             int hq;
             st = variant_config(Hmax, g.mode, g.tc, true, n_max, MP_max, dev, 0, g.fn, g.threads, g.smem, g.bps, hq);
             g.nw = g.threads / 32;
+            g.hq = hq;
+            if (!st && g.tc && g.mode == PRISM_MODE_ADMM) {
+                // the group's tiling (the members' own tiling choices do not apply to plans)
+                int t2 = 0;
+                for (SolveParams &sp : g.params) {
+                    sp.flat = g.nw == 16 ? 64 : 8 * g.nw;
+                    sp.ntiles = solve_ntiles(sp.N, sp.J, sp.flat);
+                    sp.tile0 = t2;
+                    t2 += sp.ntiles;
+                }
+                g.lp.ntiles = t2;
+                if (!g.params.empty()) g.lp.one = g.params[0];
+            }
             if (st) break;
             if (!g.params.empty()) {
                 cudaError_t e = dev_malloc(&g.d_params, sizeof(SolveParams) * g.params.size());
@@ -3046,7 +3704,16 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             for (int k : g.members) Hmax = std::max(Hmax, probs[k].h->H);
             std::vector<std::pair<bool, int>> cands;
             if (can_switch) cands.push_back({!g.tc, 0});
-            if (g.tc && g.mode == PRISM_MODE_ADMM) cands.push_back({true, g.nw == 4 ? 8 : 4});
+            // the eight-quarter kernel reads the handles' eight-quarter operand, which
+            // the factor builds only where that kernel is the default (52 < H <= 104)
+            // (and is built for one quarter length: every member must share it)
+            bool all_q8 = true;
+            for (int k : g.members)
+                all_q8 = all_q8 && probs[k].h->d_Khi8 != nullptr && probs[k].h->d_Klo8 != nullptr &&
+                         q8_hq(probs[k].h->H) == q8_hq(Hmax);
+            if (g.tc && g.mode == PRISM_MODE_ADMM)
+                for (int nw : {4, 8, 16})
+                    if (nw != g.nw && (nw != 16 || (all_q8 && q8_hq(Hmax) > 0))) cands.push_back({true, nw});
             for (const auto &cd : cands) {
                 PlanGroup alt = g;
                 alt.tc = cd.first;
@@ -3056,8 +3723,9 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
                                     alt.threads, alt.smem, alt.bps, hq);
                 if (st) break;
                 alt.nw = alt.threads / 32;
+                alt.hq = hq;
                 // the kernel's tiling: its own descriptor table
-                const int flat = (alt.tc && alt.mode == PRISM_MODE_ADMM) ? 8 * alt.nw : 0;
+                const int flat = (alt.tc && alt.mode == PRISM_MODE_ADMM) ? (alt.nw == 16 ? 64 : 8 * alt.nw) : 0;
                 int tiles = 0;
                 for (SolveParams &sp : alt.params) {
                     sp.flat = flat;
@@ -3086,7 +3754,7 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
                 }
                 if (ms2 < ms) {
                     cudaFree(g.d_params);
-                    g.tc = alt.tc; g.nw = alt.nw; g.threads = alt.threads; g.fn = alt.fn; g.smem = alt.smem;
+                    g.tc = alt.tc; g.nw = alt.nw; g.hq = alt.hq; g.threads = alt.threads; g.fn = alt.fn; g.smem = alt.smem;
                     g.bps = alt.bps; g.lp = alt.lp; g.params = alt.params; g.d_params = alt.d_params;
                     ms = ms2;
                 } else {
@@ -3194,6 +3862,8 @@ prism_status prism_proj_destroy(prism_proj_t h)
     cudaFree(h->d_wfull);
     cudaFree(h->d_Khi);
     cudaFree(h->d_Klo);
+    cudaFree(h->d_Khi8);
+    cudaFree(h->d_Klo8);
     cudaFree(h->d_err);
     cudaFree(h->d_work);
     cudaFree(h->d_stage);
@@ -3205,6 +3875,18 @@ void prism_test_fail_allocs(int skip, int count)
 {
     g_alloc_skip = skip > 0 ? skip : 0;
     g_alloc_fail = count > 0 ? count : 0;
+}
+
+prism_status prism_proj_set_tiling(prism_proj_t h, int warps)
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    if (warps != 0 && warps != 4 && warps != 8 && warps != 16)
+        return fail(PRISM_ERR_INVALID_ARG, "tiling %d: expected 0, 4, 8 or 16 warps", warps);
+    if (warps == 16 && !q8_capable(h->H))
+        return fail(PRISM_ERR_UNSUPPORTED, "eight-quarter tiles need 52 < H <= 104 (H = %d)", h->H);
+    h->tiling = warps;
+    return PRISM_OK;
 }
 
 prism_status prism_test_set_device_flag(prism_proj_t h, int value)

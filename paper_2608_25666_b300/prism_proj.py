@@ -88,6 +88,8 @@ def lib() -> ctypes.CDLL:
             L.prism_test_fail_allocs.restype = None
             L.prism_test_set_device_flag.argtypes = [P, i]
             L.prism_test_set_device_flag.restype = i
+            L.prism_proj_set_tiling.argtypes = [P, i]
+            L.prism_proj_set_tiling.restype = i
             for name in ("create", "factor", "solve", "solve_ex", "solve_plain", "solve_host",
                          "check_fp64", "shift_state", "get_factor", "query", "device_status", "destroy"):
                 getattr(L, "prism_proj_" + name).restype = i
@@ -325,6 +327,11 @@ class Projector:
         kb = np.zeros(self.H)
         _check(lib().prism_proj_get_factor(self._h, _ptr(K), _ptr(kb)))
         return K, kb
+
+    def set_tiling(self, warps: int):
+        """prism_proj_set_tiling: 0 default, 4 / 8 (four quarters), 16 (eight quarters)."""
+        _check(lib().prism_proj_set_tiling(self._h, int(warps)))
+        return self
 
     def query(self, batch: int) -> dict:
         out = (ctypes.c_longlong * 8)()
