@@ -40,11 +40,18 @@ PRECS = {"fp32": 0, "tf32x3": 3}
 # again.
 # ncu pipe utilisation of the same launch (sm__pipe_*_cycles_active and issue
 # activity, % of peak sustained), keyed like MEASURED_TRAFFIC.
-MEASURED_PIPES = {}
+MEASURED_PIPES = {
+    "tf32x3": {"kernel_source_sha256_16": "47f871d026050b07", "issue_active_pct": 57.6,
+               "sm__pipe_tensor_cycles_active_pct": 38.8, "sm__pipe_fma_cycles_active_pct": 36.1,
+               "sm__inst_executed_pipe_alu_pct": 40.3},
+    "fp32": {"kernel_source_sha256_16": "47f871d026050b07", "issue_active_pct": 61.5,
+             "sm__pipe_tensor_cycles_active_pct": 0.0, "sm__pipe_fma_cycles_active_pct": 43.1,
+             "sm__inst_executed_pipe_alu_pct": 20.3},
+}
 
 MEASURED_TRAFFIC = {
-    "fp32": {"kernel_source_sha256_16": "a1725e577f0a6b70", "bytes": 9912576},
-    "tf32x3": {"kernel_source_sha256_16": "5f5358680ac5c901", "bytes": 9950208},
+    "fp32": {"kernel_source_sha256_16": "47f871d026050b07", "bytes": 9911296},
+    "tf32x3": {"kernel_source_sha256_16": "47f871d026050b07", "bytes": 10239744},
 }
 
 
@@ -734,7 +741,8 @@ def main():
     peak = peak_fp32_tflops(q["num_sms"], 2032.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": measured_traffic(args.prec),
-                "kernel": f"solve_kernel (persistent ADMM, K-apply {args.prec})",
+                "kernel": ("solve_kernel (persistent ADMM, K-apply on the FP32 pipe)" if args.prec == "fp32"
+                           else f"solve_kernel_z (persistent ADMM, paired-FP32 rows, K-apply {args.prec})"),
                 "peak_basis": f"FP32 FMA issue rate {q['num_sms']} SMs x 128 lanes x 2 flop x 2032 MHz"
                               " (max SM clock; derived, no measured FP32 peak)",
                 "algorithmic_flops_per_launch": flops,
