@@ -350,6 +350,53 @@ def run_batched(args):
     flops = sum(pr.N * pr.J * iters * flops_per_column_iteration(pr.H) for pr in probs)
     achieved = flops / (statistics.mean(per) / 1e3) / 1e12
     peak = peak_fp32_tflops(info["num_sms"], 2032.0)
+    plan.close()
+
+    def timed_arm(step, n_steps):
+        """Per-step CUDA-event times (ms) of ``step`` after one untimed step."""
+        step()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps + 1)]
+        barrier(ws)
+        evs[0].record(stream)
+        for k in range(n_steps):
+            step()
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        return [evs[k].elapsed_time(evs[k + 1]) for k in range(n_steps)]
+
+    def arm_line(ms, how):
+        tot = barrier_max(ws, sum(ms))
+        return {"value": ws * ntraj * len(ms) / (tot / 1e3), "unit": UNIT, "steps": len(ms),
+                "ms_per_step": tot / len(ms), "p50_ms": float(np.percentile(ms, 50)),
+                "p99_ms": float(np.percentile(ms, 99)), "solver": how}
+
+    # ---- plain arm: every problem through the plain single-batch FP32 comparator,
+    # one prism_proj_solve_plain per problem on the same stream, same inputs
+    def plain_step():
+        for it in items:
+            if it["samples"].shape[0] > 0:
+                it["proj"].solve_plain(it["q0"], it["v0"], it["samples"], iters, out=it["out"],
+                                       primal=it["primal"], dual=it["dual"], stream=stream)
+    plain_arm = arm_line(timed_arm(plain_step, args.arm_steps),
+                         "prism_proj_solve_plain per problem (the plain FP32 comparator), one stream")
+
+    # ---- FP32-pipe arm: the same plan with every problem factored for the FP32-pipe
+    # K-apply (no tensor cores), graph replay, no autotuning
+    fp32_arm = None
+    if args.prec != "fp32":
+        fitems = []
+        for pr, it in zip(probs, items):
+            Pf = pp.Projector(pr.J, pr.H, pr.dt, pr.bounds).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM,
+                                                                    pp.PREC_FP32)
+            fitems.append(dict(it, proj=Pf))
+        fplan = pp.Plan(fitems, iters, autotune=False, graph=True)
+        fp32_arm = arm_line(timed_arm(lambda: fplan.launch(stream), args.arm_steps),
+                            "the same plan with the K-apply on the FP32 pipe (CUDA-graph replay)")
+        fplan.close()
+        for it in fitems:
+            it["proj"].close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
                 "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -364,9 +411,12 @@ def run_batched(args):
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": None,
                              "peak_basis": "FP32 FMA issue rate, 2032 MHz (derived)"},
-                "plan": info, "plan_build_s": plan_s, "clocks": clocks}
+                "plan": info, "plan_build_s": plan_s, "clocks": clocks,
+                "plain_arm": plain_arm, "speedup_vs_plain": plain_arm["ms_per_step"] / (total_ms / K)}
+        if fp32_arm is not None:
+            line["fp32_pipe_arm"] = fp32_arm
+            line["speedup_vs_fp32_pipe"] = fp32_arm["ms_per_step"] / (total_ms / K)
         print(json.dumps(line), flush=True)
-    plan.close()
     for it in items:
         it["proj"].close()
     return 0
@@ -566,6 +616,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=16)
+    ap.add_argument("--arm-steps", type=int, default=3, help="batched: timed steps of the comparison arms")
     ap.add_argument("--e2e-steps", type=int, default=32)
     ap.add_argument("--prec", default="tf32x3", choices=list(PRECS))
     ap.add_argument("--workload", default="realistic", choices=["realistic", "batched", "serving", "precision", "sigma_eff"])
@@ -678,7 +729,8 @@ def main():
     plain_ms = [pe[s].elapsed_time(pe[s + 1]) for s in range(args.plain_steps)]
     plain_value = w.N * args.plain_steps / (pe[0].elapsed_time(pe[-1]) / 1e3)
 
-    # ---- end to end through the host-buffer C-ABI call (pinned host memory)
+    # ---- end to end through the host-buffer C-ABI call (pinned host memory, which
+    # the solve reads and writes in place through its device mapping)
     hx = [torch.from_numpy(workloads.make_batch(w, step=rank * N_INPUTS + s)["xi"]).pin_memory()
           for s in range(4)]
     hq0 = torch.from_numpy(workloads.make_batch(w, step=0)["q0"]).pin_memory()
@@ -776,7 +828,9 @@ def main():
                 "fp32_pipe": fp32_pipe,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-                        "api": "prism_proj_solve_host (pinned host buffers, one call per step)"},
+                        "api": "prism_proj_solve_host on pinned host buffers, one call per step (the solve "
+                               "reads xi from and writes x and the residuals into the mapped host buffers: "
+                               "the bytes cross the bus inside the kernel, overlapping other tiles' iterations)"},
                 "e2e_pipelined": {"value": e2e_pipe_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                                   "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                                   "api": "prism_proj_solve on two streams, pinned-host copies around "

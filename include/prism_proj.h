@@ -137,6 +137,12 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
  *   for all iterations.  Boundary values outside the velocity bounds make the
  *   problem infeasible; they are not detected at enqueue time (they live in
  *   device memory) and show as primal_res >= their violation.
+ *   "device" buffers are any memory the device can address: device memory, or
+ *   page-locked host memory mapped into the device's address space (its device
+ *   address; with unified addressing the host pointer itself).  samples and
+ *   out are each read and written exactly once, tile by tile, in address
+ *   order, so mapped host buffers stream over the bus while other tiles
+ *   iterate (prism_proj_solve_host uses this).
  */
 prism_status prism_proj_solve(prism_proj_t h, int batch, const float *q0, const float *v0,
                               const float *samples, int iters, double rho, float *out,
@@ -201,12 +207,18 @@ prism_status prism_proj_solve_plain(prism_proj_t h, int batch, const float *q0, 
                                     float *primal_res, float *dual_res, void *cuda_stream);
 
 /*
- * prism_proj_solve_host -- end-to-end call on HOST buffers: copies q0, v0 and
- * samples (host float arrays, layouts as above; pinned memory gives the
- * fastest copies) to device staging buffers owned by the handle, runs
- * prism_proj_solve, copies x (and the residuals when the pointers are not
- * NULL) back to host memory, and synchronises cuda_stream before returning.
- * A device-side wait that ran out during the solve returns PRISM_ERR_TIMEOUT.
+ * prism_proj_solve_host -- end-to-end call on HOST buffers (host float
+ * arrays, layouts as above).  q0 and v0 are copied to a device staging buffer
+ * owned by the handle.  When samples and out are both page-locked and mapped
+ * into this device's address space (cudaHostAlloc, pinned torch tensors,
+ * cudaHostRegister with cudaHostRegisterMapped), the solve reads xi from and
+ * writes x into them directly, so the transfers overlap the iteration of the
+ * other tiles; samples == out is allowed.  Otherwise samples are copied to the
+ * staging buffer, solved in place there and x is copied back.  Each residual
+ * array (when not NULL) is written directly if mapped, else copied back.
+ * Synchronises cuda_stream before returning; a device-side wait that ran out
+ * during the solve returns PRISM_ERR_TIMEOUT.  Host buffers must not be
+ * freed or unpinned before the call returns.
  */
 prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_host,
                                    const float *v0_host, const float *samples_host, int iters,

@@ -436,6 +436,93 @@ __device__ __forceinline__ ColBounds col_bounds(const double *__restrict__ bnd, 
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
+// A tile of flattened columns [C0, C0 + Ct) (column n*J + j is joint j of
+// sample n; Ct >= 1) of an [N][H][J] array lies inside the contiguous range of
+// its whole samples nf .. nl.  Thread t walks elements t, t + nth, .. of that
+// range with (sample, step, joint) counters stepped by nth (no division in the
+// loop) and touches the elements whose column is in the tile, so a warp's
+// accesses are consecutive addresses (what host memory read or written over
+// PCIe needs) and the edge samples' other joints are skipped, not read.
+struct TileWalk {
+    int e, s, k, j;        // element of the range, its sample (from nf), step, joint
+    int dj, dk, ds;        // nth as joint, step and sample increments
+    int total, c_off;      // elements of the range; column of (s, j) = s*J + j - c_off
+};
+
+__host__ __device__ inline TileWalk tile_walk(int C0, int Ct, int H, int J, int tid, int nth)
+{
+    TileWalk w;
+    const int nf = C0 / J, nl = (C0 + Ct - 1) / J;
+    w.total = (nl - nf + 1) * H * J;
+    w.c_off = C0 - nf * J;
+    w.e = tid;
+    w.j = tid % J;
+    const int t = tid / J;
+    w.k = t % H;
+    w.s = t / H;
+    w.dj = nth % J;
+    const int tq = nth / J;
+    w.dk = tq % H;
+    w.ds = tq / H;
+    return w;
+}
+
+__host__ __device__ inline void tile_walk_next(TileWalk &w, int H, int J, int nth)
+{
+    w.e += nth;
+    w.j += w.dj;
+    const int c1 = w.j >= J;
+    if (c1) w.j -= J;
+    w.k += w.dk + c1;
+    const int c2 = w.k >= H;
+    if (c2) w.k -= H;
+    w.s += w.ds + c2;
+}
+
+// The tile's columns of src into slab rows k + 2 (row stride CP floats), up to
+// eight loads in flight per thread before their stores (src may be host memory,
+// a bus round trip away).
+__device__ __forceinline__ void load_tile_cols(const float *__restrict__ src, float *xs, int CP, int C0, int Ct,
+                                               int H, int J, int tid, int nth)
+{
+    TileWalk w = tile_walk(C0, Ct, H, J, tid, nth);
+    const float *base = src + (size_t)(C0 / J) * H * J;
+    constexpr int U = 8;
+    while (w.e < w.total) {
+        float v[U];
+        int at[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            at[u] = -1;
+            v[u] = 0.0f;
+            if (w.e < w.total) {
+                const int cc = w.s * J + w.j - w.c_off;
+                if ((unsigned)cc < (unsigned)Ct) {
+                    v[u] = __ldg(base + w.e);
+                    at[u] = (w.k + 2) * CP + cc;
+                }
+                tile_walk_next(w, H, J, nth);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (at[u] >= 0) xs[at[u]] = v[u];
+    }
+}
+
+// Slab rows k + 2 back to the tile's columns of dst.
+__device__ __forceinline__ void store_tile_cols(float *__restrict__ dst, const float *xs, int CP, int C0, int Ct,
+                                                int H, int J, int tid, int nth)
+{
+    TileWalk w = tile_walk(C0, Ct, H, J, tid, nth);
+    float *base = dst + (size_t)(C0 / J) * H * J;
+#pragma unroll 4
+    for (; w.e < w.total; tile_walk_next(w, H, J, nth)) {
+        const int cc = w.s * J + w.j - w.c_off;
+        if ((unsigned)cc < (unsigned)Ct) base[w.e] = xs[(w.k + 2) * CP + cc];
+    }
+}
+
 // 1/||Fh_r||_2 for the violation normalisation.
 __device__ __forceinline__ float inv_norm_pos(int i) { return rsqrtf((float)(i + 1)); }
 
@@ -1665,13 +1752,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
                 }
             }
         } else {
-            const float *src = p.x_init ? p.x_init : p.xi;
-            const int total = Ct * H;
-            for (int e = tid; e < total; e += NTH) {
-                const int k = e / Ct, cc = e - k * Ct;
-                const int col = C0 + cc, nn = col / J, j = col - nn * J;
-                xs[(k + 2) * CP + cc] = __ldg(src + ((size_t)nn * H + k) * J + j);
-            }
+            load_tile_cols(p.x_init ? p.x_init : p.xi, xs, CP, C0, Ct, H, J, tid, NTH);
         }
         __syncthreads();
         // ---- a2: bounds, x^0 (x_0 := v0), the halo and the prefix over earlier quarters
@@ -1990,14 +2071,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
 #pragma unroll
         for (int r = 0; r < HQ; ++r) xs[(i0 + r + 2) * CP + c] = rowof(X, r);
         __syncthreads();
-        {
-            const int total = Ct * H;
-            for (int e = tid; e < total; e += NTH) {
-                const int k = e / Ct, cc = e - k * Ct;
-                const int col = C0 + cc, nn = col / J, j = col - nn * J;
-                p.out[((size_t)nn * H + k) * J + j] = xs[(k + 2) * CP + cc];
-            }
-        }
+        store_tile_cols(p.out, xs, CP, C0, Ct, H, J, tid, NTH);
     }
     // after a timeout the MMAs of the last commit may still be running: one more
     // bounded wait for that phase before the tensor memory is freed
@@ -2199,13 +2273,7 @@ solve_kernel_q8(const __grid_constant__ LaunchParams P)
                 }
             }
         } else {
-            const float *src = p.x_init ? p.x_init : p.xi;
-            const int total = Ct * H;
-            for (int e = tid; e < total; e += NTH) {
-                const int k = e / Ct, cc = e - k * Ct;
-                const int col = C0 + cc, nn = col / J, j = col - nn * J;
-                xs[(k + 2) * CP + cc] = __ldg(src + ((size_t)nn * H + k) * J + j);
-            }
+            load_tile_cols(p.x_init ? p.x_init : p.xi, xs, CP, C0, Ct, H, J, tid, NTH);
         }
         __syncthreads();
         // ---- a2: bounds, x^0 (x_0 := v0), the halo and the sum over earlier quarters
@@ -2515,14 +2583,7 @@ solve_kernel_q8(const __grid_constant__ LaunchParams P)
             if (p.primal) p.primal[col] = fmaxf(red[c * 8], red[c * 8 + 1]);
             if (p.dual) p.dual[col] = fmaxf(red[c * 8 + 2], red[c * 8 + 3]);
         }
-        {
-            const int total = Ct * H;
-            for (int e = tid; e < total; e += NTH) {
-                const int k = e / Ct, cc = e - k * Ct;
-                const int col = C0 + cc, nn = col / J, j = col - nn * J;
-                p.out[((size_t)nn * H + k) * J + j] = xs[(k + 2) * CP + cc];
-            }
-        }
+        store_tile_cols(p.out, xs, CP, C0, Ct, H, J, tid, NTH);
     }
     if (aborted && tid == 0) (void)mbar_wait(smem_addr(&mma_bar), mma_phase ^ 1u);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -3409,6 +3470,30 @@ prism_status prism_proj_solve_plain_noalloc(prism_proj_t h, int batch, const flo
     return PRISM_OK;
 }
 
+// The device address of a page-locked host buffer of `bytes` bytes that is
+// mapped into this device's address space (cudaHostAlloc, pinned torch
+// tensors, cudaHostRegister with the mapped flag), else nullptr: pageable
+// memory, another device's mapping, or a range whose last byte is not in the
+// same mapping.
+static void *mapped_host(const void *ptr, size_t bytes, int device)
+{
+    if (!ptr || bytes == 0) return nullptr;
+    cudaPointerAttributes a, z;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || a.device != device) return nullptr;
+    const char *last = static_cast<const char *>(ptr) + bytes - 1;
+    if (cudaPointerGetAttributes(&z, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (z.type != cudaMemoryTypeHost || static_cast<char *>(z.devicePointer) != static_cast<char *>(a.devicePointer) + bytes - 1)
+        return nullptr;
+    return a.devicePointer;
+}
+
 prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_host, const float *v0_host,
                                    const float *samples_host, int iters, double rho, float *out_host,
                                    float *primal_res_host, float *dual_res_host, void *cuda_stream)
@@ -3420,7 +3505,15 @@ prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_ho
     if (!q0_host || !v0_host || !samples_host || !out_host) return fail(PRISM_ERR_INVALID_ARG, "null host pointer");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const size_t seq = (size_t)batch * h->H * h->J, cols = (size_t)batch * h->J;
-    const size_t need = seq + 2 * cols + 2 * (size_t)h->J + 8;
+    // page-locked, mapped buffers are read and written by the solve itself (its
+    // tiles stream them over the bus while other tiles iterate); the others go
+    // through a device staging buffer with one copy each way
+    const float *xi_m = static_cast<const float *>(mapped_host(samples_host, sizeof(float) * seq, h->device));
+    float *out_m = static_cast<float *>(mapped_host(out_host, sizeof(float) * seq, h->device));
+    float *pr_m = static_cast<float *>(mapped_host(primal_res_host, sizeof(float) * cols, h->device));
+    float *du_m = static_cast<float *>(mapped_host(dual_res_host, sizeof(float) * cols, h->device));
+    const bool stage_x = !xi_m || !out_m;
+    const size_t need = (stage_x ? seq : 0) + 2 * cols + 2 * (size_t)h->J + 8;
     if (need > h->stage_elems) {
         if (h->d_stage) {
             CUDA_TRY(cudaStreamSynchronize(s));
@@ -3433,20 +3526,30 @@ prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_ho
         h->d_stage = sg;
         h->stage_elems = need;
     }
-    float *d_x = h->d_stage;                 // samples in, trajectories out (in place)
-    float *d_pr = d_x + seq;
+    float *d_x = h->d_stage;                        // staged samples in, trajectories out (in place)
+    float *d_pr = d_x + (stage_x ? seq : 0);
     float *d_du = d_pr + cols;
     float *d_q0 = d_du + cols;
     float *d_v0 = d_q0 + h->J;
     CUDA_TRY(cudaMemcpyAsync(d_q0, q0_host, sizeof(float) * h->J, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(d_v0, v0_host, sizeof(float) * h->J, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(d_x, samples_host, sizeof(float) * seq, cudaMemcpyHostToDevice, s));
-    st = prism_proj_solve(h, batch, d_q0, d_v0, d_x, iters, rho, d_x, primal_res_host ? d_pr : nullptr,
-                          dual_res_host ? d_du : nullptr, cuda_stream);
+    const float *xin = xi_m;
+    float *xout = out_m;
+    if (stage_x) {
+        // one side pageable: the solve runs in place on the staging buffer
+        CUDA_TRY(cudaMemcpyAsync(d_x, samples_host, sizeof(float) * seq, cudaMemcpyHostToDevice, s));
+        xin = d_x;
+        xout = d_x;
+    }
+    float *pr = primal_res_host ? (pr_m ? pr_m : d_pr) : nullptr;
+    float *du = dual_res_host ? (du_m ? du_m : d_du) : nullptr;
+    st = prism_proj_solve(h, batch, d_q0, d_v0, xin, iters, rho, xout, pr, du, cuda_stream);
     if (st) return st;
-    CUDA_TRY(cudaMemcpyAsync(out_host, d_x, sizeof(float) * seq, cudaMemcpyDeviceToHost, s));
-    if (primal_res_host) CUDA_TRY(cudaMemcpyAsync(primal_res_host, d_pr, sizeof(float) * cols, cudaMemcpyDeviceToHost, s));
-    if (dual_res_host) CUDA_TRY(cudaMemcpyAsync(dual_res_host, d_du, sizeof(float) * cols, cudaMemcpyDeviceToHost, s));
+    if (stage_x) CUDA_TRY(cudaMemcpyAsync(out_host, d_x, sizeof(float) * seq, cudaMemcpyDeviceToHost, s));
+    if (primal_res_host && !pr_m)
+        CUDA_TRY(cudaMemcpyAsync(primal_res_host, d_pr, sizeof(float) * cols, cudaMemcpyDeviceToHost, s));
+    if (dual_res_host && !du_m)
+        CUDA_TRY(cudaMemcpyAsync(dual_res_host, d_du, sizeof(float) * cols, cudaMemcpyDeviceToHost, s));
     return prism_proj_device_status(h, cuda_stream);
 }
 

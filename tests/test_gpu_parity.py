@@ -163,6 +163,45 @@ def test_host_buffer_entry_point_matches_device():
     P.close()
 
 
+@pytest.mark.parametrize("prec", [pp.PREC_TF32X3, pp.PREC_FP32], ids=["tc", "simt"])
+@pytest.mark.parametrize("J,H,N,dt", [(12, 50, 50, 0.02), (7, 33, 37, 0.05), (1, 20, 45, 0.05)])
+@pytest.mark.parametrize("how", ["pinned", "pinned_in_place", "pinned_in_pageable_out"])
+def test_host_entry_point_on_pinned_buffers(prec, J, H, N, dt, how):
+    """Page-locked host buffers are read and written by the solve itself (the
+    tiles stream them over the bus); a pageable side falls back to staging.
+    Every form equals the solve on device buffers bit for bit (same kernel,
+    same inputs), including in place (samples is out), and the device result
+    matches the oracle."""
+    import torch
+    b = workloads.make_custom(11 + J, N, J, H, dt)
+    P = pp.Projector(J, H, dt, b["bounds"]).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, prec)
+    xi, q0, v0 = to_dev(b)
+    xd, pd, dd = P.solve(q0, v0, xi, 40)
+    torch.cuda.synchronize()
+    hx = torch.from_numpy(b["xi"]).pin_memory()
+    hq0, hv0 = torch.from_numpy(b["q0"]).pin_memory(), torch.from_numpy(b["v0"]).pin_memory()
+    hpr = torch.full((N, J), float("nan")).pin_memory()
+    hdu = torch.full((N, J), float("nan")).pin_memory()
+    if how == "pinned":
+        hout = torch.full((N, H, J), float("nan")).pin_memory()
+    elif how == "pinned_in_place":
+        hout = hx
+    else:
+        hout = np.full((N, H, J), np.nan, dtype=np.float32)
+    xo, pr, du = P.solve_host(hq0, hv0, hx, 40, out=hout, primal=hpr, dual=hdu)
+    xo = xo.numpy() if isinstance(xo, torch.Tensor) else xo
+    assert np.array_equal(xo, xd.cpu().numpy())
+    assert np.array_equal(pr.numpy(), pd.cpu().numpy()) and np.array_equal(du.numpy(), dd.cpu().numpy())
+    if how != "pinned_in_place":
+        assert np.array_equal(hx.numpy(), b["xi"])      # the samples are left alone
+    g = {"x": xd.cpu().numpy().astype(np.float64), "primal": pd.cpu().numpy().astype(np.float64),
+         "dual": dd.cpu().numpy().astype(np.float64)}
+    ncols = N * J
+    cols = np.unique(np.linspace(0, ncols - 1, min(ncols, 16)).astype(np.int64))
+    assert_parity(g, oracle_solve(b, 40, 1.0, cols=cols), cols=cols, dual_tol=2e-4)
+    P.close()
+
+
 def test_fp64_check_matches_oracle_residual():
     import torch
     b = workloads.make_custom(8, 30, 12, 30, 0.05)
