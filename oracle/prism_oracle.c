@@ -344,8 +344,10 @@ static void solve_column(const setup_t *S, const double *bnd, double q0, double 
     oracle_build_G_h(H, S->dt, bnd, q0, v0, G0, h);
     free(G0);
 
+    /* x_1 is the boundary value (Eq. proj_boundary) in every iterate, the
+     * starting one included: a warm start's first step is replaced by v0 */
     for (int i = 0; i < H; ++i) x[i] = x_init ? x_init[i] : xi[i];
-    if (!x_init) x[0] = v0;
+    x[0] = v0;
     memcpy(xprev, x, sizeof(double) * H);
 
     if (S->mode == ORACLE_MODE_PAPER) {
@@ -437,7 +439,8 @@ static void solve_column(const setup_t *S, const double *bnd, double q0, double 
  *   bounds   [8][J]
  *   q0, v0   [J]
  *   xi       [N][H][J]
- *   x_init   [N][H][J] or NULL;   dual_init [N][D][J] or NULL,
+ *   x_init   [N][H][J] or NULL (its first step is replaced by v0);
+ *            dual_init [N][D][J] or NULL,
  *            D = 4H-1 (ADMM, scaled multiplier u') or H (PAPER, lambda)
  *   x_out    [N][H][J];  primal, dual [N][J];  dual_out [N][D][J] or NULL
  *   cols     optional list of flattened columns n*J + j to solve (others are

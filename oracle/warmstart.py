@@ -45,8 +45,10 @@ def features(xi, q0, v0, bounds):
 
 
 def design(F, W1, b1):
-    """Phi = [max(0, F W1^T + b1) | F]."""
+    """Phi = [max(0, F W1^T + b1) | F]; Phi = F without a hidden layer (W1 None)."""
     F = np.asarray(F, dtype=np.float64)
+    if W1 is None:
+        return F.copy()
     W1 = np.asarray(W1, dtype=np.float64).reshape(-1, F.shape[1])
     b1 = np.asarray(b1, dtype=np.float64).reshape(W1.shape[0])
     h = np.maximum(F @ W1.T + b1[None, :], 0.0)

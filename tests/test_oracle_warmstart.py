@@ -61,6 +61,12 @@ def test_identity_first_layer_is_the_positive_part():
     assert np.array_equal(Phi[:, 7:], F)
 
 
+def test_no_hidden_layer_is_the_linear_model():
+    rng = np.random.default_rng(8)
+    F = rng.normal(size=(20, 6))
+    assert np.array_equal(ws.design(F, None, None), F)
+
+
 def test_target_layout():
     N, H, J = 3, 4, 2
     D = 4 * H - 1
@@ -115,3 +121,21 @@ def test_fitted_model_beats_a_cold_start():
                               x_init=xw, dual_init=dw)
     assert np.max(warm["primal"]) < 0.7 * np.max(cold["primal"])
     assert np.max(np.abs(warm["x"] - ref["x"])) < 0.7 * np.max(np.abs(cold["x"] - ref["x"]))
+
+
+def test_warm_start_first_step_is_the_boundary_value():
+    """x_1 = v0 (Eq. proj_boundary) holds for the starting iterate too: a warm
+    start whose first step differs from v0 gives the result of one whose first
+    step is v0."""
+    H, dt = 15, 0.05
+    b = workloads.make_custom(31, 6, 3, H, dt)
+    rng = np.random.default_rng(9)
+    x0 = rng.normal(size=(6, H, 3))
+    u0 = rng.normal(size=(6, 4 * H - 1, 3))
+    x0v = x0.copy()
+    x0v[:, 0, :] = b["v0"][None, :]
+    a = oracle.solve_batch(b["xi"], b["q0"], b["v0"], b["bounds"], dt, 7, 1.0, x_init=x0, dual_init=u0,
+                           want_dual_state=True)
+    c = oracle.solve_batch(b["xi"], b["q0"], b["v0"], b["bounds"], dt, 7, 1.0, x_init=x0v, dual_init=u0,
+                           want_dual_state=True)
+    assert np.array_equal(a["x"], c["x"]) and np.array_equal(a["dual_state"], c["dual_state"])
