@@ -486,6 +486,83 @@ void prism_test_fail_allocs(int skip, int count);
  */
 prism_status prism_test_set_device_flag(prism_proj_t h, int value);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start of the projection (the neural warm-starting of the
+ * projection QP that the paper's conclusion lists as future work; it gives no
+ * model, so the model is this library's reading).  Per column c = n*J + j a
+ * network with a fixed first layer and a linear skip maps the d = H + 3
+ * features
+ *   f_k = xi[n][k][j] / vmax_j (k < H),  f_H = v0_j / vmax_j,
+ *   f_{H+1} = (q0_j - (qmin_j + qmax_j)/2) / ((qmax_j - qmin_j)/2),  f_{H+2} = 1
+ * (bounds of the handle) to phi = [max(0, W1 f + b1) | f] (K2 = hidden + d)
+ * and y_hat = phi W2 = [u' | x]: the ADMM-mode multiplier in the units of
+ * prism_proj_solve_ex's dual_init (D = 4H - 1 rows) and the trajectory, to be
+ * passed as that call's dual_init and x_init.  W2 [K2][D + H] is fitted by
+ * ridge regression on converged solves:
+ *   (Phi^T Phi / n + lambda I) W2 = Phi^T Y / n   (FP64).
+ * ------------------------------------------------------------------------ */
+typedef struct prism_ws_s *prism_ws_t;
+
+/*
+ * prism_ws_create -- a warm-start model for a handle factored in ADMM mode
+ * (else PRISM_ERR_NOT_FACTORED / PRISM_ERR_INVALID_ARG).  The handle must
+ * outlive the model.
+ *   hidden  width of the first layer: a multiple of 16 in [0, 128] (0: the
+ *           linear model phi = f)
+ *   W1_host, b1_host  host double [hidden][H+3] and [hidden], copied (the
+ *           caller draws them; may be NULL when hidden = 0)
+ *   On success *out holds the model; on failure *out is NULL.  Synchronous.
+ */
+prism_status prism_ws_create(prism_proj_t h, int hidden, const double *W1_host, const double *b1_host,
+                             prism_ws_t *out);
+
+/*
+ * prism_ws_accumulate -- add a batch's columns to the fit's sums Phi^T Phi and
+ * Phi^T Y (FP64, on the device).
+ *   q0, v0    device float [J]; samples device float [N][H][J] (as prism_proj_solve)
+ *   x_star    device float [N][H][J]: the converged trajectories of these samples
+ *   dual_star device float [N][D][J]: their multiplier, as prism_proj_solve_ex
+ *             exports it (dual_out)
+ * Enqueued on cuda_stream; the model keeps a design-row workspace of up to
+ * 65536 columns x (K2 + D + H) doubles.
+ */
+prism_status prism_ws_accumulate(prism_ws_t w, int batch, const float *q0, const float *v0, const float *samples,
+                                 const float *x_star, const float *dual_star, void *cuda_stream);
+
+/*
+ * prism_ws_fit -- solve for W2 with ridge parameter lambda >= 0 (Cholesky in
+ * FP64 on the device) and prepare the predictor's operands.  Synchronises
+ * cuda_stream.  A matrix that is not positive definite (lambda = 0 with too few
+ * or collinear columns) returns PRISM_ERR_INVALID_ARG and leaves no model.
+ * The sums stay, so more batches can be added and the model refitted.
+ */
+prism_status prism_ws_fit(prism_ws_t w, double lambda, void *cuda_stream);
+
+/*
+ * prism_ws_predict -- the fitted model on a batch: x_init device float
+ * [N][H][J] and dual_init device float [N][D][J] for prism_proj_solve_ex.
+ * Runs on the tensor cores with bf16 operands and FP32 accumulation (the
+ * prediction is a starting point, the solve sets the accuracy).  Enqueued on
+ * cuda_stream; a bounded device-side wait that ran out raises the handle's
+ * timeout flag (prism_proj_device_status).  Before a successful fit:
+ * PRISM_ERR_NOT_FACTORED.
+ */
+prism_status prism_ws_predict(prism_ws_t w, int batch, const float *q0, const float *v0, const float *samples,
+                              float *x_init, float *dual_init, void *cuda_stream);
+
+/*
+ * prism_ws_get -- synchronous copies for inspection: S = Phi^T Phi host double
+ * [K2][K2], T = Phi^T Y host double [K2][D+H], W2 host double [K2][D+H] (after
+ * a fit) and the number of accumulated columns; any pointer may be NULL.
+ */
+prism_status prism_ws_get(prism_ws_t w, double *S_host, double *T_host, double *W2_host, long long *n_out);
+
+/* prism_ws_reset -- clear the sums (the fitted model stays until the next fit). */
+prism_status prism_ws_reset(prism_ws_t w);
+
+/* prism_ws_destroy -- free the model (synchronises the device). */
+prism_status prism_ws_destroy(prism_ws_t w);
+
 /* prism_proj_destroy -- free the handle and its device memory (synchronises the device). */
 prism_status prism_proj_destroy(prism_proj_t h);
 

@@ -1,7 +1,7 @@
 """Build step of libprism_proj: nvcc for sm_103a, in-tree output.
 
 ``python -m paper_2608_25666_b300.build`` (or ``build()``) compiles
-``csrc/prism_proj.cu`` into ``_build/libprism_proj.so``.  nvcc cross-compiles
+``csrc/*.cu``, ``csrc/prism_server.cpp`` into ``_build/libprism_proj.so``.  nvcc cross-compiles
 without a GPU, so this runs on any machine with the CUDA toolkit.
 """
 from __future__ import annotations
@@ -16,7 +16,9 @@ ROOT = os.path.dirname(_HERE)
 SRC = os.path.join(_HERE, "csrc", "prism_proj.cu")
 SRC_SERVER = os.path.join(_HERE, "csrc", "prism_server.cpp")
 SRC_MPPI = os.path.join(_HERE, "csrc", "prism_mppi.cu")
-SOURCES = [SRC, SRC_MPPI, SRC_SERVER]
+SRC_WS = os.path.join(_HERE, "csrc", "prism_ws.cu")
+SOURCES = [SRC, SRC_MPPI, SRC_SERVER, SRC_WS]
+HEADERS = [os.path.join(_HERE, "csrc", "tcgen05_common.cuh")]
 HDR = os.path.join(ROOT, "include", "prism_proj.h")
 OUT = os.path.join(_HERE, "_build", "libprism_proj.so")
 
@@ -33,7 +35,7 @@ def nvcc() -> str:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    newest = max([os.path.getmtime(f) for f in SOURCES] + [os.path.getmtime(HDR)])
+    newest = max([os.path.getmtime(f) for f in SOURCES + HEADERS] + [os.path.getmtime(HDR)])
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= newest:
         return OUT
     tmp = OUT + f".tmp{os.getpid()}"

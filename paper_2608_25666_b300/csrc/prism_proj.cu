@@ -33,6 +33,7 @@
 //   y = Fh x;  p = y + clip(y);  g = Fh^T (w p);  rhs = rho g + lambda + xi;
 //   x <- K rhs + kb v0;  lambda <- lambda - (rho/2) Fh^T w (2 Fh x - p).
 #include "prism_proj.h"
+#include "tcgen05_common.cuh"
 
 #include <cuda_runtime.h>
 
@@ -678,26 +679,16 @@ __device__ __forceinline__ void kapply(float *__restrict__ xs, const float *__re
 }
 
 // ===========================================================================
-// tcgen05 helpers (Blackwell tensor cores, accumulator in tensor memory).
-// Operands are K-major, no swizzle: element (r, k) of an R x KD tf32 matrix
-// lives at byte ((r/8)*(KD/4) + k/4)*128 + (r%8)*16 + (k%4)*4, i.e. 8-row x
-// 16-byte core matrices, K-adjacent ones 128 B apart (LBO), 8-row groups
-// (KD/4)*128 B apart (SBO).
+// tcgen05 helpers (Blackwell tensor cores, accumulator in tensor memory; the
+// generic ones are in tcgen05_common.cuh).  Operands are K-major, no swizzle:
+// element (r, k) of an R x KD tf32 matrix lives at byte
+// ((r/8)*(KD/4) + k/4)*128 + (r%8)*16 + (k%4)*4, i.e. 8-row x 16-byte core
+// matrices, K-adjacent ones 128 B apart (LBO), 8-row groups (KD/4)*128 B apart
+// (SBO).
 // ===========================================================================
 __host__ __device__ __forceinline__ int cm_off(int r, int k, int KD)
 {
     return ((r >> 3) * (KD >> 2) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4;
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version of tcgen05; no swizzle, base offset 0
-    return d;
 }
 
 // kind::tf32 instruction descriptor: D f32, A and B tf32, both K-major.
@@ -729,33 +720,10 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t 
                  :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void umma_commit(uint32_t mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
-}
-
 // Programmatic dependent launch: the grid launched after this one on the stream
 // with programmatic serialisation may start once every block of this one has
 // executed this (or exited).  No-op without a dependent launch.
 __device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// One lane of the (converged) warp.
-__device__ __forceinline__ bool elect_one()
-{
-    uint32_t pred = 0;
-    asm volatile("{\n.reg .pred P;\nelect.sync _|P, 0xffffffff;\nselp.u32 %0, 1, 0, P;\n}\n" : "=r"(pred));
-    return pred != 0;
-}
-
-// Bounded wait on an mbarrier phase; returns false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit = 1u << 22)
-{
-    uint32_t done = 0;
-    for (uint32_t it = 0; it < limit && !done; ++it)
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-    return done != 0;
-}
 
 // Sets (ACC = false) or adds to (ACC = true) out[k] (k < KN) this
 // quarter-thread's entries of tensor-memory columns col0 + 4k + t%4, lanes t/4
@@ -4013,4 +3981,21 @@ __attribute__((visibility("hidden"))) prism_status prism_internal_fail(prism_sta
 __attribute__((visibility("hidden"))) int *prism_internal_err_flag(prism_proj_t h)
 {
     return h ? h->d_err : nullptr;
+}
+
+// Shape, device and bounds of a handle factored in ADMM mode (the learned warm
+// start, prism_ws.cu, predicts that mode's multiplier); not part of the C ABI.
+__attribute__((visibility("hidden"))) prism_status prism_internal_admm_shape(prism_proj_t h, int *J, int *H,
+                                                                             int *device, const double **d_bounds)
+{
+    prism_status st = check_handle(h);
+    if (st) return st;
+    if (!h->factored) return fail(PRISM_ERR_NOT_FACTORED, "prism_proj_factor has not been called");
+    if (h->mode != PRISM_MODE_ADMM)
+        return fail(PRISM_ERR_INVALID_ARG, "the learned warm start predicts the ADMM-mode multiplier");
+    *J = h->J;
+    *H = h->H;
+    *device = h->device;
+    *d_bounds = h->d_bounds;
+    return PRISM_OK;
 }

@@ -118,6 +118,15 @@ def lib() -> ctypes.CDLL:
             L.prism_mppi_workspace_bytes.restype = ctypes.c_size_t
             L.prism_mppi_update.argtypes = [i, i, i, P, d, d, P, P, P, P, P, ctypes.c_size_t, P]
             L.prism_mppi_update.restype = i
+            L.prism_ws_create.argtypes = [P, i, P, P, ctypes.POINTER(P)]
+            L.prism_ws_accumulate.argtypes = [P, i, P, P, P, P, P, P]
+            L.prism_ws_fit.argtypes = [P, d, P]
+            L.prism_ws_predict.argtypes = [P, i, P, P, P, P, P, P]
+            L.prism_ws_get.argtypes = [P, P, P, P, ctypes.POINTER(ll)]
+            L.prism_ws_reset.argtypes = [P]
+            L.prism_ws_destroy.argtypes = [P]
+            for name in ("create", "accumulate", "fit", "predict", "get", "reset", "destroy"):
+                getattr(L, "prism_ws_" + name).restype = i
             L.prism_status_string.argtypes = [i]
             L.prism_status_string.restype = ctypes.c_char_p
             L.prism_last_error.argtypes = []
@@ -472,6 +481,89 @@ class Server:
             _check(lib().prism_server_destroy(self._h))
             self._h = None
             self._refs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class WarmStart:
+    """Learned warm start of an ADMM-mode Projector (prism_ws_*): a fixed random
+    first layer (W1 [hidden][H+3], b1 [hidden]; drawn here from ``seed`` unless
+    given) with a linear skip, output layer fitted by ridge regression on
+    converged solves, evaluated on the tensor cores."""
+
+    def __init__(self, proj: "Projector", hidden: int = 64, seed: int = 0, W1=None, b1=None):
+        self.proj = proj
+        self.J, self.H = proj.J, proj.H
+        self.D = 4 * self.H - 1
+        self.hidden = int(hidden)
+        d = self.H + 3
+        if self.hidden > 0 and W1 is None:
+            rng = np.random.default_rng(seed)
+            W1 = rng.normal(0.0, 1.0 / np.sqrt(d), size=(self.hidden, d))
+            b1 = rng.uniform(-1.0, 1.0, size=self.hidden)
+        self.W1 = None if W1 is None else np.ascontiguousarray(np.asarray(W1, dtype=np.float64).reshape(self.hidden, d))
+        self.b1 = None if b1 is None else np.ascontiguousarray(np.asarray(b1, dtype=np.float64).reshape(self.hidden))
+        h = ctypes.c_void_p()
+        _check(lib().prism_ws_create(proj._h, self.hidden, _ptr(self.W1), _ptr(self.b1), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def K2(self) -> int:
+        return self.hidden + self.H + 3
+
+    def accumulate(self, q0, v0, samples, x_star, dual_star, stream=None):
+        N = int(samples.shape[0])
+        _need_cuda_f32("q0", q0, (self.J,))
+        _need_cuda_f32("v0", v0, (self.J,))
+        _need_cuda_f32("samples", samples, (N, self.H, self.J))
+        _need_cuda_f32("x_star", x_star, (N, self.H, self.J))
+        _need_cuda_f32("dual_star", dual_star, (N, self.D, self.J))
+        _check(lib().prism_ws_accumulate(self._h, N, _ptr(q0), _ptr(v0), _ptr(samples), _ptr(x_star),
+                                         _ptr(dual_star), _stream_ptr(stream)))
+        return self
+
+    def fit(self, lam: float = 1e-3, stream=None):
+        _check(lib().prism_ws_fit(self._h, float(lam), _stream_ptr(stream)))
+        return self
+
+    def predict(self, q0, v0, samples, x_init=None, dual_init=None, stream=None):
+        """(x_init [N][H][J], dual_init [N][D][J]) on the device."""
+        import torch
+        N = int(samples.shape[0])
+        _need_cuda_f32("q0", q0, (self.J,))
+        _need_cuda_f32("v0", v0, (self.J,))
+        _need_cuda_f32("samples", samples, (N, self.H, self.J))
+        if x_init is None:
+            x_init = torch.empty((N, self.H, self.J), dtype=torch.float32, device=samples.device)
+        if dual_init is None:
+            dual_init = torch.empty((N, self.D, self.J), dtype=torch.float32, device=samples.device)
+        _need_cuda_f32("x_init", x_init, (N, self.H, self.J))
+        _need_cuda_f32("dual_init", dual_init, (N, self.D, self.J))
+        _check(lib().prism_ws_predict(self._h, N, _ptr(q0), _ptr(v0), _ptr(samples), _ptr(x_init),
+                                      _ptr(dual_init), _stream_ptr(stream)))
+        return x_init, dual_init
+
+    def get(self, want_w2: bool = True):
+        """Host copies: dict(S [K2][K2], T [K2][D+H], W2 or None, n)."""
+        K2, NO = self.K2, self.D + self.H
+        S = np.empty((K2, K2))
+        T = np.empty((K2, NO))
+        W2 = np.empty((K2, NO)) if want_w2 else None
+        n = ctypes.c_longlong()
+        _check(lib().prism_ws_get(self._h, _ptr(S), _ptr(T), _ptr(W2), ctypes.byref(n)))
+        return {"S": S, "T": T, "W2": W2, "n": int(n.value)}
+
+    def reset(self):
+        _check(lib().prism_ws_reset(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().prism_ws_destroy(self._h)
+            self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:
