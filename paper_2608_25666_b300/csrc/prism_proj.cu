@@ -172,6 +172,7 @@ struct prism_proj_s {
     float *d_wp = nullptr;               // [PRISM_MAX_H] position-row weights
     float *d_Khi = nullptr, *d_Klo = nullptr;   // [n+4][n+4] tf32 split of [K' | kb' | C] + quarter-prefix rows
     float *d_Khi8 = nullptr, *d_Klo8 = nullptr; // [n+8][n+22] eight-quarter operand (52 < H <= 104, tensor cores)
+    float *d_Bz = nullptr, *d_Wz = nullptr;     // solve_kernel_z's B operand and weight pairs, shared-memory layout
     int *d_err = nullptr;                // tensor-core wait timeout flag
     int tiling = 0;                      // prism_proj_set_tiling: 0 default, 4 / 8 / 16 warps
     double *d_wfull = nullptr;           // factor input: per-row weights (4 blocks x H)
@@ -385,6 +386,8 @@ struct SolveParams {
     const float *__restrict__ Klo;       // [n+4][n+4] remainder - Khi
     const float *__restrict__ Khi8;      // [n+8][n+22] tf32 high part of the eight-quarter operand (or NULL)
     const float *__restrict__ Klo8;      // its remainder
+    const float *__restrict__ Bz;        // solve_kernel_z's operand B in its shared-memory layout (staged at factor)
+    const float *__restrict__ Wz;        // solve_kernel_z's weight pairs in their shared-memory layout
     int *err;                            // set to 1 if a tensor-core wait ran out
     const float *x_init;                 // [N][H][J] warm-start iterate or NULL (x^0 = xi)
     const float *dual_init;              // [N][D][J] warm-start multiplier or NULL (0)
@@ -1545,6 +1548,78 @@ __host__ __device__ inline ZSmem solve_smem_z(int hq, int nw)
 // horizon chunk) the four quarters' rows of a column fall 8 banks apart.
 __host__ __device__ constexpr int z_col_stride(int nw) { return 8 * nw + 8; }
 
+// 16-byte copy global -> shared (both 16-byte aligned, bytes a multiple of 16),
+// U loads in flight per thread.
+template <int U>
+__device__ __forceinline__ void copy16_smem(unsigned char *dst, const void *src, int bytes, int tid, int nth)
+{
+    const uint4 *s = static_cast<const uint4 *>(src);
+    uint4 *t = reinterpret_cast<uint4 *>(dst);
+    const int n16 = bytes >> 4;
+    for (int i0 = tid; i0 < n16; i0 += U * nth) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * nth;
+            if (i < n16) v[u] = __ldg(s + i);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * nth;
+            if (i < n16) t[i] = v[u];
+        }
+    }
+}
+
+// Loads in flight per thread in solve_kernel_z's operand copy (registers there
+// are at their limit).
+#ifndef ZCOPY
+#define ZCOPY 1
+#endif
+
+// solve_kernel_z's per-problem operand B = [K' | kb' | C] split in tf32 high /
+// low parts (rows = D columns in the interleaved output order, then the four
+// quarter-prefix rows; K = the right-hand-side slots, v0 in quarter 0's spare
+// slot, the quarter totals in the others'), and its weight pairs (zero on rows
+// that do not exist), written once per factor in the kernel's shared-memory
+// layout: Bz[cm_off(row, k, KD) / 4], Wz[kind][quarter][pair].
+__global__ void stage_z_kernel(int HQ, int n, int H, const float *__restrict__ Khi, const float *__restrict__ Klo,
+                               const float *__restrict__ wp, float wa0, float wa, float wj0, float wj,
+                               float *__restrict__ Bz, float *__restrict__ Wz)
+{
+    const int KD = tc_kd(HQ), ND = tc_nrows(HQ), HQ4 = tc_hq4(HQ), NP = (HQ + 1) / 2;
+    const int KW = n + 4;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int e = t0; e < 2 * ND * KD; e += nt) {
+        const int pr = e / KD, kq = e - pr * KD;
+        const bool low = pr >= ND;
+        const int pc = low ? pr - ND : pr;
+        const int xt = (pc & 3) * HQ + (pc >> 2);   // time step of D column pc
+        const bool prefix = pc >= 4 * HQ;           // column 4HQ + b: quarter b's prefix sum
+        const int i = prefix ? n + (pc & 3) : xt - 1;
+        const int kb_ = kq / HQ4, kr = kq - kb_ * HQ4;
+        const int rr = (kr & ~3) | ((kr & 3) ^ kb_);  // local row stored in this slot
+        const int xk = kb_ * HQ + rr;
+        int j = -1;
+        if (rr < HQ) j = (xk >= 1 && xk <= n) ? xk - 1 : -1;
+        else if (rr == HQ) j = (kb_ == 0) ? n : n + kb_;
+        const bool in = (prefix || (xt >= 1 && xt <= n)) && j >= 0;
+        const int src = i * KW + j;
+        Bz[cm_off(pr, kq, KD) >> 2] = in ? (low ? Klo[src] : Khi[src]) : 0.0f;
+    }
+    for (int e = t0; e < 3 * 8 * NP; e += nt) {
+        const int kind = e / (8 * NP), rem = e - kind * 8 * NP;
+        const int bq = rem / (2 * NP), r = rem - bq * 2 * NP;
+        const int i = bq * HQ + r;
+        const bool ex = r < HQ && i < H;
+        float w = 0.0f;
+        if (kind == 0) w = ex ? wp[i] : 0.0f;
+        else if (kind == 1) w = ex ? (i == 0 ? wa0 : wa) : 0.0f;
+        else w = (ex && i >= 1) ? (i == 1 ? wj0 : wj) : 0.0f;
+        Wz[e] = w;
+    }
+}
+
 // Resident blocks per SM the kernel is compiled for: 128 registers a thread up
 // to the chunk of 17 steps, 255 beyond.
 template <int HQ, int NW>
@@ -1646,7 +1721,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
             pi = lo;
         }
         const SolveParams &p = BATCHED ? P.many[pi] : P.one;
-        const int H = p.H, J = p.J, n = p.n;
+        const int H = p.H, J = p.J;
         const int HJ = H * J;
         const float rho = p.rho;
         const int iters = p.iters, polish = p.polish;
@@ -1655,42 +1730,11 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
         const int Ct = min(CM, p.N * J - C0);
         __syncthreads();   // previous tile fully stored before the slab is overwritten
         if (pi != cur) {
-            // per-problem operand B = [K' | kb' | C] split in tf32 high / low parts
-            // (rows = D columns in the interleaved output order, then the four
-            // quarter-prefix rows; K = this problem's right-hand-side slots, v0 in
-            // quarter 0's spare slot, the quarter totals in the others') and the
-            // weight pairs (zero on rows that do not exist)
-            const int KW = n + 4;
-            for (int e = tid; e < 2 * ND * KD; e += NTH) {
-                const int pr = e / KD, kq = e - pr * KD;
-                const bool low = pr >= ND;
-                const int pc = low ? pr - ND : pr;
-                const int xt = (pc & 3) * HQ + (pc >> 2);   // time step of D column pc
-                const bool prefix = pc >= 4 * HQ;           // column 4HQ + b: quarter b's prefix sum
-                const int i = prefix ? n + (pc & 3) : xt - 1;
-                const int kb_ = kq / HQ4, kr = kq - kb_ * HQ4;
-                const int rr = (kr & ~3) | ((kr & 3) ^ kb_);  // local row stored in this slot
-                const int xk = kb_ * HQ + rr;
-                int j = -1;
-                if (rr < HQ) j = (xk >= 1 && xk <= n) ? xk - 1 : -1;
-                else if (rr == HQ) j = (kb_ == 0) ? n : n + kb_;
-                const bool in = (prefix || (xt >= 1 && xt <= n)) && j >= 0;
-                const int src = i * KW + j;
-                *reinterpret_cast<float *>(smem_raw + L.bhi + cm_off(pr, kq, KD)) =
-                    in ? (low ? p.Klo[src] : p.Khi[src]) : 0.0f;
-            }
-            float *wt = reinterpret_cast<float *>(smem_raw + L.wt);
-            for (int e = tid; e < 3 * 8 * NP; e += NTH) {
-                const int kind = e / (8 * NP), rem = e - kind * 8 * NP;
-                const int bq = rem / (2 * NP), r = rem - bq * 2 * NP;
-                const int i = bq * HQ + r;
-                const bool ex = r < HQ && i < H;
-                float w = 0.0f;
-                if (kind == 0) w = ex ? p.wp[i] : 0.0f;
-                else if (kind == 1) w = ex ? (i == 0 ? p.wa0 : p.wa) : 0.0f;
-                else w = (ex && i >= 1) ? (i == 1 ? p.wj0 : p.wj) : 0.0f;
-                wt[e] = w;
-            }
+            // per-problem operand B = [K' | kb' | C] (tf32 high parts over low parts,
+            // with the quarter-prefix rows) and the weight pairs, staged at factor
+            // time in this layout (stage_z_kernel): plain 16-byte copies
+            copy16_smem<ZCOPY>(smem_raw + L.bhi, p.Bz, 2 * ND * KD * 4, tid, NTH);
+            copy16_smem<ZCOPY>(smem_raw + L.wt, p.Wz, 3 * 8 * NP * 4, tid, NTH);
             cur = pi;
         }
         // ---- a1: the tile's columns of xi (or x_init, or the drawn samples) into rows 2..H+1
@@ -2894,6 +2938,7 @@ prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const flo
     p.Kt = h->d_Kt32; p.kb = h->d_kb32; p.wp = h->d_wp;
     p.Khi = h->d_Khi; p.Klo = h->d_Klo; p.err = h->d_err;
     p.Khi8 = h->d_Khi8; p.Klo8 = h->d_Klo8;
+    p.Bz = h->d_Bz; p.Wz = h->d_Wz;
     p.x_init = nullptr; p.dual_init = nullptr; p.dual_out = nullptr;
     p.D = (h->mode == PRISM_MODE_ADMM) ? 4 * h->H - 1 : h->H;
     p.tile0 = 0;
@@ -3248,7 +3293,12 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
         if (e == cudaSuccess) e = dev_malloc(&Klo, sizeof(float) * (n + 4) * (n + 4));
         if (e == cudaSuccess) e = dev_malloc(&err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
-        float *Khi8 = nullptr, *Klo8 = nullptr;
+        float *Khi8 = nullptr, *Klo8 = nullptr, *Bz = nullptr, *Wz = nullptr;
+        const Variant *zv = pick_variant(H);
+        if (e == cudaSuccess && zv && tc_fits(H)) {
+            e = dev_malloc(&Bz, sizeof(float) * 2 * tc_nrows(zv->hq) * tc_kd(zv->hq));
+            if (e == cudaSuccess) e = dev_malloc(&Wz, sizeof(float) * 3 * 8 * ((zv->hq + 1) / 2));
+        }
         if (e == cudaSuccess && q8_capable(H)) {
             e = dev_malloc(&Khi8, sizeof(float) * (n + 8) * (n + 22));
             if (e == cudaSuccess) e = dev_malloc(&Klo8, sizeof(float) * (n + 8) * (n + 22));
@@ -3256,12 +3306,14 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
         if (e != cudaSuccess) {
             cudaFree(K64); cudaFree(kb64); cudaFree(Kt32); cudaFree(kb32); cudaFree(wp);
             cudaFree(wfull); cudaFree(Khi); cudaFree(Klo); cudaFree(err); cudaFree(Khi8); cudaFree(Klo8);
+            cudaFree(Bz); cudaFree(Wz);
             return fail(e == cudaErrorMemoryAllocation ? PRISM_ERR_OOM : PRISM_ERR_CUDA, "factor buffers: %s",
                         cudaGetErrorString(e));
         }
         h->d_K64 = K64; h->d_kb64 = kb64; h->d_Kt32 = Kt32; h->d_kb32 = kb32; h->d_wp = wp;
         h->d_wfull = wfull; h->d_Khi = Khi; h->d_Klo = Klo; h->d_err = err;
         h->d_Khi8 = Khi8; h->d_Klo8 = Klo8;
+        h->d_Bz = Bz; h->d_Wz = Wz;
     }
     const Weights w = make_weights(scale, h->dt);
     double wfull[4 * PRISM_MAX_H];
@@ -3284,6 +3336,11 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
     factor_kernel<<<1, 256, smem, s>>>(H, rho_c, h->d_wfull, h->d_K64, h->d_kb64, h->d_Kt32, h->d_kb32, MP,
                                        h->d_Khi, h->d_Klo, fv->hq, h->d_Khi8, h->d_Klo8, q8_hq(H));
     CUDA_TRY(cudaGetLastError());
+    if (h->d_Bz) {
+        stage_z_kernel<<<32, 256, 0, s>>>(fv->hq, n, H, h->d_Khi, h->d_Klo, h->d_wp, (float)w.wa0, (float)w.wa,
+                                         (float)w.wj0, (float)w.wj, h->d_Bz, h->d_Wz);
+        CUDA_TRY(cudaGetLastError());
+    }
     // the host tables above are stack memory: make sure the copies completed
     CUDA_TRY(cudaStreamSynchronize(s));
     h->factored = true;
@@ -3935,6 +3992,8 @@ prism_status prism_proj_destroy(prism_proj_t h)
     cudaFree(h->d_Klo);
     cudaFree(h->d_Khi8);
     cudaFree(h->d_Klo8);
+    cudaFree(h->d_Bz);
+    cudaFree(h->d_Wz);
     cudaFree(h->d_err);
     cudaFree(h->d_work);
     cudaFree(h->d_stage);

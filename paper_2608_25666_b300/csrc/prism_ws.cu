@@ -60,6 +60,8 @@ struct prism_ws_s {
     long long zcap = 0;
     long long n = 0;                     // columns accumulated
     bool fitted = false;
+    int smem = 0, max_grid = 0;          // the predictor's launch configuration (set at create)
+    int w2_resident = 0;                 // W2 kept in shared memory for the whole launch
 };
 
 namespace {
@@ -137,6 +139,28 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8])
                  :: "memory");
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Thread t of warp w: tensor-memory lane 32 w + t, columns col .. col + 31
+// (one load, one wait).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                   "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
@@ -319,7 +343,7 @@ __global__ void ws_pack_kernel(const double *__restrict__ src, int rows, int col
 // The predictor.
 // ---------------------------------------------------------------------------
 struct WsPredictParams {
-    int ncols, J, H, D, NO, NOP, d, K1, hidden, K2P, ntiles;
+    int ncols, J, H, D, NO, NOP, d, K1, hidden, K2P, ntiles, w2_resident;
     const double *bnd;
     const float *q0, *v0, *xi;
     const uint16_t *W1p, *W2p;
@@ -328,27 +352,43 @@ struct WsPredictParams {
     int *err;
 };
 
+// Shared memory of the predictor: W1 (bf16 [hidden][K1]), the output layer's A
+// operand [phi | f] (bf16 [TM][K2P]; its f columns are also the hidden layer's
+// A operand), and W2: all of it (resident) or one chunk of NCH outputs.
 struct WsSmem {
-    int w1, a1, a2, w2, total;
+    int w1, a2, w2, total;
 };
 
-__host__ __device__ inline WsSmem ws_smem(int hidden, int K1, int K2P)
+__host__ __device__ inline WsSmem ws_smem(int hidden, int K1, int K2P, int NOP, bool resident)
 {
     WsSmem L;
     int off = 0;
     L.w1 = off; off += hidden * K1 * 2;
-    L.a1 = off; off += TM * K1 * 2;
     L.a2 = off; off += TM * K2P * 2;
-    L.w2 = off; off += NCH * K2P * 2;
+    L.w2 = off; off += (resident ? NOP : NCH) * K2P * 2;
     L.total = off;
     return L;
 }
 
+// 16-byte copy global -> shared, eight loads in flight per thread.
 __device__ __forceinline__ void copy16(unsigned char *dst, const void *src, int bytes, int tid, int nth)
 {
     const uint4 *s = static_cast<const uint4 *>(src);
     uint4 *t = reinterpret_cast<uint4 *>(dst);
-    for (int i = tid; i < (bytes >> 4); i += nth) t[i] = __ldg(s + i);
+    const int n16 = bytes >> 4;
+    for (int i0 = tid; i0 < n16; i0 += 8 * nth) {
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * nth;
+            if (i < n16) v[u] = __ldg(s + i);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * nth;
+            if (i < n16) t[i] = v[u];
+        }
+    }
 }
 
 __device__ __forceinline__ uint32_t tcols_for(int hidden) { return hidden > NCH ? 256u : 128u; }
@@ -359,8 +399,8 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
     __shared__ uint32_t tslot;
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const WsSmem L = ws_smem(P.hidden, P.K1, P.K2P);
-    unsigned char *W1s = sm + L.w1, *A1 = sm + L.a1, *A2 = sm + L.a2, *W2s = sm + L.w2;
+    const WsSmem L = ws_smem(P.hidden, P.K1, P.K2P, P.NOP, P.w2_resident != 0);
+    unsigned char *W1s = sm + L.w1, *A2 = sm + L.a2, *W2s = sm + L.w2;
     const uint32_t TC = tcols_for(P.hidden);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_addr(&tslot)), "r"(TC));
@@ -371,6 +411,8 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (P.hidden > 0) copy16(W1s, P.W1p, P.hidden * P.K1 * 2, tid, TM);
+    if (P.w2_resident) copy16(W2s, P.W2p, P.NOP * P.K2P * 2, tid, TM);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -378,13 +420,14 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
     const uint32_t tl = tbase + ((uint32_t)(32 * warp) << 16);
     uint32_t phase = 0;
     bool aborted = false;
-    const uint32_t sbo1 = (uint32_t)(P.K1 >> 3) * 128u, sbo2 = (uint32_t)(P.K2P >> 3) * 128u;
+    const uint32_t sbo2 = (uint32_t)(P.K2P >> 3) * 128u;
 
     for (int tile = blockIdx.x; tile < P.ntiles && !aborted; tile += gridDim.x) {
         const int c = tile * TM + tid;
         const bool valid = c < P.ncols;
         const int n = valid ? c / P.J : 0, j = valid ? c - n * P.J : 0;
-        // ---- features of this thread's column, bf16, into A1 (row tid) and the skip part of A2
+        // ---- features of this thread's column, bf16, into the f columns of A2 (row
+        // tid); 32 loads in flight
         {
             float fv0 = 0.0f, fq0 = 0.0f;
             float inv_v = 0.0f;
@@ -395,10 +438,10 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
                 fq0 = (float)jf.fq0;
             }
             const float *xs = P.xi + (size_t)n * P.H * P.J + j;
-            for (int k0 = 0; k0 < P.K1; k0 += 8) {
-                float f[8];
+            for (int k0 = 0; k0 < P.K1; k0 += 32) {
+                float f[32];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < 32; ++i) {
                     const int k = k0 + i;
                     float v = 0.0f;
                     if (valid) {
@@ -409,22 +452,27 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
                     }
                     f[i] = v;
                 }
-                const uint4 q = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
-                                           pack_bf16x2(f[6], f[7]));
-                *reinterpret_cast<uint4 *>(A1 + cm16(tid, k0, P.K1)) = q;
-                *reinterpret_cast<uint4 *>(A2 + cm16(tid, P.hidden + k0, P.K2P)) = q;
+#pragma unroll
+                for (int g = 0; g < 32; g += 8) {
+                    if (k0 + g < P.K1) {
+                        const uint4 q = make_uint4(pack_bf16x2(f[g], f[g + 1]), pack_bf16x2(f[g + 2], f[g + 3]),
+                                                   pack_bf16x2(f[g + 4], f[g + 5]), pack_bf16x2(f[g + 6], f[g + 7]));
+                        *reinterpret_cast<uint4 *>(A2 + cm16(tid, P.hidden + k0 + g, P.K2P)) = q;
+                    }
+                }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        // ---- hidden layer: D[:, 0:hidden] = A1 W1^T, then h = max(0, D + b1) into A2
+        // ---- hidden layer: D[:, 0:hidden] = F W1^T (F: the f columns of A2, same
+        // row-group stride), then h = max(0, D + b1) into the first columns of A2
         if (P.hidden > 0) {
             if (warp == 0) {
                 if (elect_one()) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint64_t da = umma_desc(smem_addr(A1), 128u, sbo1);
-                    const uint64_t db = umma_desc(smem_addr(W1s), 128u, sbo1);
+                    const uint64_t da = umma_desc(smem_addr(A2 + cm16(0, P.hidden, P.K2P)), 128u, sbo2);
+                    const uint64_t db = umma_desc(smem_addr(W1s), 128u, (uint32_t)(P.K1 >> 3) * 128u);
                     const uint32_t id = idesc_bf16(TM, P.hidden);
                     for (int ks = 0; ks < (P.K1 >> 4); ++ks)
                         umma_bf16(tbase, da + (uint64_t)(16 * ks), db + (uint64_t)(16 * ks), id, ks > 0 ? 1u : 0u);
@@ -439,14 +487,25 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int g = 0; g < P.hidden; g += 8) {
-                float v[8];
-                tmem_ld8(tl + (uint32_t)g, v);
+            for (int g0 = 0; g0 < P.hidden; g0 += 32) {
+                float v[32];
+                if (g0 + 32 <= P.hidden) {
+                    tmem_ld32(tl + (uint32_t)g0, v);
+                } else {
+                    tmem_ld8(tl + (uint32_t)g0, v);
+                    tmem_ld8(tl + (uint32_t)g0 + 8u, v + 8);
+                }
 #pragma unroll
-                for (int i = 0; i < 8; ++i) v[i] = fmaxf(v[i] + __ldg(P.b1 + g + i), 0.0f);
-                const uint4 q = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                                           pack_bf16x2(v[6], v[7]));
-                *reinterpret_cast<uint4 *>(A2 + cm16(tid, g, P.K2P)) = q;
+                for (int g = 0; g < 32; g += 8) {
+                    if (g0 + g < P.hidden) {
+                        float h[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) h[i] = fmaxf(v[g + i] + __ldg(P.b1 + g0 + g + i), 0.0f);
+                        const uint4 q = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]),
+                                                   pack_bf16x2(h[4], h[5]), pack_bf16x2(h[6], h[7]));
+                        *reinterpret_cast<uint4 *>(A2 + cm16(tid, g0 + g, P.K2P)) = q;
+                    }
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -455,15 +514,18 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
         // ---- output layer in chunks of NCH outputs: D[:, 0:nw] = A2 W2[o0 : o0 + nw]^T
         for (int o0 = 0; o0 < P.NOP; o0 += NCH) {
             const int nw = min(NCH, P.NOP - o0);
-            copy16(W2s, P.W2p + (size_t)o0 * P.K2P, nw * P.K2P * 2, tid, TM);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
+            unsigned char *W2c = W2s + (P.w2_resident ? (size_t)o0 * P.K2P * 2 : 0);
+            if (!P.w2_resident) {
+                copy16(W2s, P.W2p + (size_t)o0 * P.K2P, nw * P.K2P * 2, tid, TM);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+            }
             if (warp == 0) {
                 if (elect_one()) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint64_t da = umma_desc(smem_addr(A2), 128u, sbo2);
-                    const uint64_t db = umma_desc(smem_addr(W2s), 128u, sbo2);
+                    const uint64_t db = umma_desc(smem_addr(W2c), 128u, sbo2);
                     const uint32_t id = idesc_bf16(TM, nw);
                     for (int ks = 0; ks < (P.K2P >> 4); ++ks)
                         umma_bf16(tbase, da + (uint64_t)(16 * ks), db + (uint64_t)(16 * ks), id, ks > 0 ? 1u : 0u);
@@ -478,15 +540,23 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int g = 0; g < nw; g += 8) {
-                float v[8];
-                tmem_ld8(tl + (uint32_t)g, v);
+            for (int g = 0; g < nw; g += 32) {
+                float v[32];
+                if (g + 32 <= nw) {
+                    tmem_ld32(tl + (uint32_t)g, v);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; q += 8)
+                        if (g + q < nw) tmem_ld8(tl + (uint32_t)(g + q), v + q);
+                }
                 if (valid) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
+                    for (int i = 0; i < 32; ++i) {
                         const int o = o0 + g + i;
-                        if (o < P.D) P.dual_init[((size_t)n * P.D + o) * P.J + j] = v[i];
-                        else if (o < P.NO) P.x_init[((size_t)n * P.H + (o - P.D)) * P.J + j] = v[i];
+                        if (g + i < nw) {
+                            if (o < P.D) P.dual_init[((size_t)n * P.D + o) * P.J + j] = v[i];
+                            else if (o < P.NO) P.x_init[((size_t)n * P.H + (o - P.D)) * P.J + j] = v[i];
+                        }
                     }
                 }
             }
@@ -565,11 +635,32 @@ prism_status prism_ws_create(prism_proj_t h, int hidden, const double *W1_host, 
     w->ZW = w->K2 + w->NO;
     w->device = device;
     w->d_bounds = bnd;
-    const WsSmem L = ws_smem(hidden, w->K1, w->K2P);
-    if (L.total > 227 * 1024) {
+    // the predictor's launch configuration: W2 resident in shared memory when two
+    // blocks still fit an SM, else streamed in chunks; blocks per SM from shared
+    // memory and from tensor memory (512 columns per SM)
+    int smem_sm = 0, smem_blk = 0, reserved = 0, sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
         delete w;
-        return wfail(PRISM_ERR_UNSUPPORTED, "predictor shared memory %d B exceeds 227 KB", L.total);
+        return wfail(PRISM_ERR_CUDA, "device attributes: %s", cudaGetErrorString(e));
     }
+    const int static_smem = 64;   // the kernel's own __shared__ words, rounded up
+    const auto per_sm_of = [&](int dyn) {
+        return std::min(smem_sm / (dyn + static_smem + reserved), 512 / (int)(hidden > NCH ? 256 : 128));
+    };
+    const WsSmem Lr = ws_smem(hidden, w->K1, w->K2P, w->NOP, true);
+    const WsSmem Ls = ws_smem(hidden, w->K1, w->K2P, w->NOP, false);
+    w->w2_resident = Lr.total <= smem_blk && per_sm_of(Lr.total) >= 2;
+    const WsSmem L = w->w2_resident ? Lr : Ls;
+    if (L.total > smem_blk) {
+        delete w;
+        return wfail(PRISM_ERR_UNSUPPORTED, "predictor shared memory %d B exceeds %d B", L.total, smem_blk);
+    }
+    w->smem = L.total;
+    w->max_grid = std::max(1, per_sm_of(L.total)) * sms;
     if ((st = ws_alloc(&w->d_W1, (size_t)hidden * w->d)) || (st = ws_alloc(&w->d_b1, hidden)) ||
         (st = ws_alloc(&w->d_b1f, hidden)) || (st = ws_alloc(&w->d_W1p, (size_t)std::max(hidden, 16) * w->K1)) ||
         (st = ws_alloc(&w->d_W2p, (size_t)w->NOP * w->K2P)) || (st = ws_alloc(&w->d_G, (size_t)w->K2 * w->ZW)) ||
@@ -578,7 +669,6 @@ prism_status prism_ws_create(prism_proj_t h, int hidden, const double *W1_host, 
         free_ws(w);
         return st;
     }
-    cudaError_t e = cudaSuccess;
     if (hidden > 0) {
         float b1f[WS_MAX_HIDDEN];
         for (int i = 0; i < hidden; ++i) b1f[i] = (float)b1_host[i];
@@ -590,6 +680,10 @@ prism_status prism_ws_create(prism_proj_t h, int hidden, const double *W1_host, 
             e = cudaGetLastError();
         }
     }
+    // the predictor's launch configuration, once: its shared memory, and the
+    // resident blocks (shared memory, and 512 tensor-memory columns per SM)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ws_predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, w->smem);
     if (e == cudaSuccess) e = cudaMemset(w->d_G, 0, sizeof(double) * w->K2 * w->ZW);
     if (e == cudaSuccess) e = cudaMemset(w->d_W2p, 0, sizeof(uint16_t) * w->NOP * w->K2P);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -684,6 +778,7 @@ prism_status prism_ws_predict(prism_ws_t w, int batch, const float *q0, const fl
     p.K1 = w->K1;
     p.hidden = w->hidden;
     p.K2P = w->K2P;
+    p.w2_resident = w->w2_resident;
     p.ntiles = (p.ncols + TM - 1) / TM;
     p.bnd = w->d_bounds;
     p.q0 = q0;
@@ -695,15 +790,8 @@ prism_status prism_ws_predict(prism_ws_t w, int batch, const float *q0, const fl
     p.x_init = x_init;
     p.dual_init = dual_init;
     p.err = prism_internal_err_flag(w->h);
-    const int smem = ws_smem(w->hidden, w->K1, w->K2P).total;
-    WS_CUDA(cudaFuncSetAttribute(ws_predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    int per_sm = 0, sms = 0;
-    WS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ws_predict_kernel, TM, smem));
-    WS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, w->device));
-    // tensor-memory columns bound the resident blocks too
-    per_sm = std::max(1, std::min(per_sm, 512 / (w->hidden > NCH ? 256 : 128)));
-    const int grid = std::max(1, std::min(p.ntiles, per_sm * sms));
-    ws_predict_kernel<<<grid, TM, smem, (cudaStream_t)cuda_stream>>>(p);
+    const int grid = std::max(1, std::min(p.ntiles, w->max_grid));
+    ws_predict_kernel<<<grid, TM, w->smem, (cudaStream_t)cuda_stream>>>(p);
     WS_CUDA(cudaGetLastError());
     return PRISM_OK;
 }
