@@ -62,6 +62,7 @@ struct prism_ws_s {
     bool fitted = false;
     int smem = 0, max_grid = 0;          // the predictor's launch configuration (set at create)
     int w2_resident = 0;                 // W2 kept in shared memory for the whole launch
+    int nch = 128;                       // outputs per output-layer MMA
 };
 
 namespace {
@@ -343,7 +344,7 @@ __global__ void ws_pack_kernel(const double *__restrict__ src, int rows, int col
 // The predictor.
 // ---------------------------------------------------------------------------
 struct WsPredictParams {
-    int ncols, J, H, D, NO, NOP, d, K1, hidden, K2P, ntiles, w2_resident;
+    int ncols, J, H, D, NO, NOP, d, K1, hidden, K2P, ntiles, w2_resident, nch;
     const double *bnd;
     const float *q0, *v0, *xi;
     const uint16_t *W1p, *W2p;
@@ -352,20 +353,21 @@ struct WsPredictParams {
     int *err;
 };
 
-// Shared memory of the predictor: W1 (bf16 [hidden][K1]), the output layer's A
-// operand [phi | f] (bf16 [TM][K2P]; its f columns are also the hidden layer's
-// A operand), and W2: all of it (resident) or one chunk of NCH outputs.
+// Shared memory of the predictor: W1 (bf16 [hidden][K1]), b1 (float), the output
+// layer's A operand [phi | f] (bf16 [TM][K2P]; its f columns are also the hidden
+// layer's A operand), and W2: all of it (resident) or one chunk of nch outputs.
 struct WsSmem {
-    int w1, a2, w2, total;
+    int w1, b1, a2, w2, total;
 };
 
-__host__ __device__ inline WsSmem ws_smem(int hidden, int K1, int K2P, int NOP, bool resident)
+__host__ __device__ inline WsSmem ws_smem(int hidden, int K1, int K2P, int NOP, bool resident, int nch)
 {
     WsSmem L;
     int off = 0;
     L.w1 = off; off += hidden * K1 * 2;
+    L.b1 = off; off += hidden * 4;
     L.a2 = off; off += TM * K2P * 2;
-    L.w2 = off; off += (resident ? NOP : NCH) * K2P * 2;
+    L.w2 = off; off += (resident ? NOP : nch) * K2P * 2;
     L.total = off;
     return L;
 }
@@ -393,14 +395,15 @@ __device__ __forceinline__ void copy16(unsigned char *dst, const void *src, int 
 
 __device__ __forceinline__ uint32_t tcols_for(int hidden) { return hidden > NCH ? 256u : 128u; }
 
-__global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant__ WsPredictParams P)
+__global__ void __launch_bounds__(TM, 4) ws_predict_kernel(const __grid_constant__ WsPredictParams P)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint32_t tslot;
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const WsSmem L = ws_smem(P.hidden, P.K1, P.K2P, P.NOP, P.w2_resident != 0);
+    const WsSmem L = ws_smem(P.hidden, P.K1, P.K2P, P.NOP, P.w2_resident != 0, P.nch);
     unsigned char *W1s = sm + L.w1, *A2 = sm + L.a2, *W2s = sm + L.w2;
+    const float *b1s = reinterpret_cast<const float *>(sm + L.b1);
     const uint32_t TC = tcols_for(P.hidden);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_addr(&tslot)), "r"(TC));
@@ -410,7 +413,10 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (P.hidden > 0) copy16(W1s, P.W1p, P.hidden * P.K1 * 2, tid, TM);
+    if (P.hidden > 0) {
+        copy16(W1s, P.W1p, P.hidden * P.K1 * 2, tid, TM);
+        copy16(sm + L.b1, P.b1, P.hidden * 4, tid, TM);
+    }
     if (P.w2_resident) copy16(W2s, P.W2p, P.NOP * P.K2P * 2, tid, TM);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -500,7 +506,7 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
                     if (g0 + g < P.hidden) {
                         float h[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) h[i] = fmaxf(v[g + i] + __ldg(P.b1 + g0 + g + i), 0.0f);
+                        for (int i = 0; i < 8; ++i) h[i] = fmaxf(v[g + i] + b1s[g0 + g + i], 0.0f);
                         const uint4 q = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]),
                                                    pack_bf16x2(h[4], h[5]), pack_bf16x2(h[6], h[7]));
                         *reinterpret_cast<uint4 *>(A2 + cm16(tid, g0 + g, P.K2P)) = q;
@@ -511,9 +517,12 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
         }
-        // ---- output layer in chunks of NCH outputs: D[:, 0:nw] = A2 W2[o0 : o0 + nw]^T
-        for (int o0 = 0; o0 < P.NOP; o0 += NCH) {
-            const int nw = min(NCH, P.NOP - o0);
+        // ---- output layer in chunks of nch outputs: D[:, 0:nw] = A2 W2[o0 : o0 + nw]^T;
+        // output o of this column: dual_init[n][o][j] (o < D), x_init[n][o - D][j]
+        float *const pd = P.dual_init + (size_t)n * P.D * P.J + j;
+        float *const px = P.x_init + (size_t)n * P.H * P.J + j;
+        for (int o0 = 0; o0 < P.NOP; o0 += P.nch) {
+            const int nw = min(P.nch, P.NOP - o0);
             unsigned char *W2c = W2s + (P.w2_resident ? (size_t)o0 * P.K2P * 2 : 0);
             if (!P.w2_resident) {
                 copy16(W2s, P.W2p + (size_t)o0 * P.K2P, nw * P.K2P * 2, tid, TM);
@@ -550,13 +559,14 @@ __global__ void __launch_bounds__(TM, 1) ws_predict_kernel(const __grid_constant
                         if (g + q < nw) tmem_ld8(tl + (uint32_t)(g + q), v + q);
                 }
                 if (valid) {
+                    const int ob = o0 + g;
+                    const int od = min(32, min(nw - g, P.D - ob));      // outputs of this group in dual_init
+                    const int oe = min(32, min(nw - g, P.NO - ob));     // outputs of this group that exist
+                    // (od <= 0 once ob >= D; ob + i - D >= 0 whenever i >= od)
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
-                        const int o = o0 + g + i;
-                        if (g + i < nw) {
-                            if (o < P.D) P.dual_init[((size_t)n * P.D + o) * P.J + j] = v[i];
-                            else if (o < P.NO) P.x_init[((size_t)n * P.H + (o - P.D)) * P.J + j] = v[i];
-                        }
+                        if (i < od) pd[(long long)(ob + i) * P.J] = v[i];
+                        else if (i < oe) px[(long long)(ob + i - P.D) * P.J] = v[i];
                     }
                 }
             }
@@ -647,20 +657,38 @@ prism_status prism_ws_create(prism_proj_t h, int hidden, const double *W1_host, 
         delete w;
         return wfail(PRISM_ERR_CUDA, "device attributes: %s", cudaGetErrorString(e));
     }
-    const int static_smem = 64;   // the kernel's own __shared__ words, rounded up
-    const auto per_sm_of = [&](int dyn) {
-        return std::min(smem_sm / (dyn + static_smem + reserved), 512 / (int)(hidden > NCH ? 256 : 128));
-    };
-    const WsSmem Lr = ws_smem(hidden, w->K1, w->K2P, w->NOP, true);
-    const WsSmem Ls = ws_smem(hidden, w->K1, w->K2P, w->NOP, false);
-    w->w2_resident = Lr.total <= smem_blk && per_sm_of(Lr.total) >= 2;
-    const WsSmem L = w->w2_resident ? Lr : Ls;
-    if (L.total > smem_blk) {
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, ws_predict_kernel);
+    if (e != cudaSuccess) {
         delete w;
-        return wfail(PRISM_ERR_UNSUPPORTED, "predictor shared memory %d B exceeds %d B", L.total, smem_blk);
+        return wfail(PRISM_ERR_CUDA, "predictor attributes: %s", cudaGetErrorString(e));
     }
-    w->smem = L.total;
-    w->max_grid = std::max(1, per_sm_of(L.total)) * sms;
+    const int static_smem = (int)fa.sharedSizeBytes;
+    const int by_regs = 65536 / (std::max(fa.numRegs, 1) * TM);
+    const auto per_sm_of = [&](int dyn) {
+        return std::min(std::min(smem_sm / (dyn + static_smem + reserved), by_regs),
+                        512 / (int)(hidden > NCH ? 256 : 128));
+    };
+    // the most resident blocks per SM; among equals W2 resident, then the widest chunk
+    int best = 0;
+    const int chunks[] = {NCH, 96, 64, 48, 32, 16};
+    for (int res = 1; res >= 0; --res)
+        for (int nc : chunks) {
+            if (res && nc != NCH) continue;
+            const int tot = ws_smem(hidden, w->K1, w->K2P, w->NOP, res != 0, nc).total;
+            const int per = tot <= smem_blk ? per_sm_of(tot) : 0;
+            if (per > best) {
+                best = per;
+                w->w2_resident = res;
+                w->nch = nc;
+                w->smem = tot;
+            }
+        }
+    if (best < 1) {
+        delete w;
+        return wfail(PRISM_ERR_UNSUPPORTED, "predictor shared memory exceeds %d B", smem_blk);
+    }
+    w->max_grid = best * sms;
     if ((st = ws_alloc(&w->d_W1, (size_t)hidden * w->d)) || (st = ws_alloc(&w->d_b1, hidden)) ||
         (st = ws_alloc(&w->d_b1f, hidden)) || (st = ws_alloc(&w->d_W1p, (size_t)std::max(hidden, 16) * w->K1)) ||
         (st = ws_alloc(&w->d_W2p, (size_t)w->NOP * w->K2P)) || (st = ws_alloc(&w->d_G, (size_t)w->K2 * w->ZW)) ||
@@ -779,6 +807,7 @@ prism_status prism_ws_predict(prism_ws_t w, int batch, const float *q0, const fl
     p.hidden = w->hidden;
     p.K2P = w->K2P;
     p.w2_resident = w->w2_resident;
+    p.nch = w->nch;
     p.ntiles = (p.ncols + TM - 1) / TM;
     p.bnd = w->d_bounds;
     p.q0 = q0;
