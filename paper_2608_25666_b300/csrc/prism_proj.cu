@@ -1521,7 +1521,7 @@ __device__ __forceinline__ void tmem_read_x(uint32_t taddr, bool split, float ou
 
 // Shared-memory carve-up of solve_kernel_z (byte offsets).
 struct ZSmem {
-    int a, bhi, xi, wt, total;
+    int a, bhi, xi, wt, cb, total;
 };
 
 // Words between two quarter-threads' xi rows: the row pairs rounded up to an odd
@@ -1540,6 +1540,7 @@ __host__ __device__ inline ZSmem solve_smem_z(int hq, int nw)
     L.bhi = off; off += 2 * ND * KD * 4;                 // B: high parts over low parts (N-stacked)
     L.xi = off;  off += 32 * nw * z_xi_stride(hq) * 4;   // xi, each quarter-thread's rows contiguous
     L.wt = off;  off += 3 * 4 * NP * 8;                  // weight pairs: position, acceleration, jerk x quarter x pair
+    L.cb = off;  off += PRISM_MAX_J * (int)sizeof(ColBounds);   // each joint's bounds, computed once per problem
     L.total = off;
     return L;
 }
@@ -1667,6 +1668,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
     float *xs = reinterpret_cast<float *>(smem_raw + L.a);   // tile slab, outside the iteration loop only
 
     const float2 *wtab = reinterpret_cast<const float2 *>(smem_raw + L.wt);
+    ColBounds *cbt = reinterpret_cast<ColBounds *>(smem_raw + L.cb);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -1735,6 +1737,9 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
             // time in this layout (stage_z_kernel): plain 16-byte copies
             copy16_smem<ZCOPY>(smem_raw + L.bhi, p.Bz, 2 * ND * KD * 4, tid, NTH);
             copy16_smem<ZCOPY>(smem_raw + L.wt, p.Wz, 3 * 8 * NP * 4, tid, NTH);
+            // the bounds of each joint (FP64 arithmetic, rounded once): one thread per
+            // joint here instead of every thread on every tile
+            if (tid < J) cbt[tid] = col_bounds(p.bounds, J, tid, p.dt, p.q0[tid], p.v0[tid]);
             cur = pi;
         }
         // ---- a1: the tile's columns of xi (or x_init, or the drawn samples) into rows 2..H+1
@@ -1771,8 +1776,8 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
         const bool colv = c < Ct;
         const int n_c = colv ? (C0 + c) / J : 0;      // sample and joint of this column
         const int jj = colv ? (C0 + c) - n_c * J : 0;
-        const float q0j = p.q0[jj], v0j = p.v0[jj];
-        const ColBounds cb = col_bounds(p.bounds, J, jj, p.dt, q0j, v0j);
+        const float v0j = p.v0[jj];
+        const ColBounds cb = cbt[jj];
         // rows with shifted bounds: acceleration row 0 and jerk row 1 of quarter 0
         const float alo_r0 = (b == 0) ? cb.alo0 : cb.alo, ahi_r0 = (b == 0) ? cb.ahi0 : cb.ahi;
         const float jlo_r1 = (b == 0) ? cb.jlo1 : cb.jlo, jhi_r1 = (b == 0) ? cb.jhi1 : cb.jhi;

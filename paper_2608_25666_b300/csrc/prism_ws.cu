@@ -49,6 +49,7 @@ struct prism_ws_s {
     double *d_W1 = nullptr;              // [hidden][d] first layer (FP64, for the fit)
     double *d_b1 = nullptr;              // [hidden]
     float *d_b1f = nullptr;              // [hidden] (FP32, for the predictor)
+    float *d_jf = nullptr;               // [J][4] per-joint feature constants: 1/vmax, q centre, 1/q half-range
     uint16_t *d_W1p = nullptr;           // bf16 [hidden][K1] core-matrix layout (B of the hidden-layer MMA)
     uint16_t *d_W2p = nullptr;           // bf16 [NOP][K2P] core-matrix layout (B of the output-layer MMA)
     double *d_G = nullptr;               // [K2][ZW] sums Phi^T [Phi | Y]
@@ -60,9 +61,8 @@ struct prism_ws_s {
     long long zcap = 0;
     long long n = 0;                     // columns accumulated
     bool fitted = false;
-    int smem = 0, max_grid = 0;          // the predictor's launch configuration (set at create)
-    int w2_resident = 0;                 // W2 kept in shared memory for the whole launch
-    int nch = 128;                       // outputs per output-layer MMA
+    int smem = 0;                        // the predictor's largest dynamic shared memory (set at create)
+    int cfg_nch[4] = {}, cfg_smem[4] = {}, cfg_per_sm[4] = {}, ncfg = 0, sms = 0;   // candidates per chunk width
 };
 
 namespace {
@@ -101,7 +101,6 @@ prism_status ws_alloc(T **p, size_t count)
 
 constexpr int WS_MAX_HIDDEN = 128;
 constexpr int TM = 128;                  // columns per predictor tile (the MMA's M)
-constexpr int NCH = 128;                 // outputs per output-layer MMA (its N)
 constexpr int ZCHUNK = 65536;            // columns per design / sum pass
 constexpr int B_QMIN = 0, B_QMAX = 1, B_VMAX = 3;   // rows of the [8][J] bounds
 
@@ -344,30 +343,32 @@ __global__ void ws_pack_kernel(const double *__restrict__ src, int rows, int col
 // The predictor.
 // ---------------------------------------------------------------------------
 struct WsPredictParams {
-    int ncols, J, H, D, NO, NOP, d, K1, hidden, K2P, ntiles, w2_resident, nch;
+    int ncols, J, H, D, NO, NOP, d, K1, hidden, K2P, ntiles, nch;
     const double *bnd;
     const float *q0, *v0, *xi;
     const uint16_t *W1p, *W2p;
     const float *b1;
+    const float *jf;       // [J][4]: 1/vmax, q centre, 1/q half-range, 0
     float *x_init, *dual_init;
     int *err;
 };
 
 // Shared memory of the predictor: W1 (bf16 [hidden][K1]), b1 (float), the output
 // layer's A operand [phi | f] (bf16 [TM][K2P]; its f columns are also the hidden
-// layer's A operand), and W2: all of it (resident) or one chunk of nch outputs.
+// layer's A operand), and two buffers for chunks of nch rows of W2.
 struct WsSmem {
-    int w1, b1, a2, w2, total;
+    int w1, b1, a2, w2a, w2b, total;
 };
 
-__host__ __device__ inline WsSmem ws_smem(int hidden, int K1, int K2P, int NOP, bool resident, int nch)
+__host__ __device__ inline WsSmem ws_smem(int hidden, int K1, int K2P, int nch)
 {
     WsSmem L;
     int off = 0;
     L.w1 = off; off += hidden * K1 * 2;
     L.b1 = off; off += hidden * 4;
     L.a2 = off; off += TM * K2P * 2;
-    L.w2 = off; off += (resident ? NOP : nch) * K2P * 2;
+    L.w2a = off; off += nch * K2P * 2;
+    L.w2b = off; off += nch * K2P * 2;
     L.total = off;
     return L;
 }
@@ -393,55 +394,117 @@ __device__ __forceinline__ void copy16(unsigned char *dst, const void *src, int 
     }
 }
 
-__device__ __forceinline__ uint32_t tcols_for(int hidden) { return hidden > NCH ? 256u : 128u; }
+// Bulk asynchronous copy global -> shared (both 16-byte aligned, bytes a
+// multiple of 16) that completes on the mbarrier, which expects its bytes.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
 
+// Tensor-memory columns of a block: the hidden layer (up to 128) and two output
+// chunks of nch <= 64 columns each.
+constexpr uint32_t WS_TCOLS = 128;
+
+// Per tile of TM columns: features -> hidden layer (one MMA chain, readback
+// with bias and ReLU) -> output layer in chunks of nch outputs, software-
+// pipelined over two W2 buffers and two accumulators: the W2 rows of chunk c+2
+// are copied (cp.async.bulk) as soon as chunk c's MMA has read its buffer, and
+// chunk c+2's MMA is issued once chunk c's accumulator has been read back, so
+// copies and MMAs overlap the readback and stores of the chunk before.
 __global__ void __launch_bounds__(TM, 4) ws_predict_kernel(const __grid_constant__ WsPredictParams P)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint32_t tslot;
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar_h, bar_ld[2], bar_mm[2];
+    __shared__ int fail;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const WsSmem L = ws_smem(P.hidden, P.K1, P.K2P, P.NOP, P.w2_resident != 0, P.nch);
-    unsigned char *W1s = sm + L.w1, *A2 = sm + L.a2, *W2s = sm + L.w2;
+    const WsSmem L = ws_smem(P.hidden, P.K1, P.K2P, P.nch);
+    unsigned char *W1s = sm + L.w1, *A2 = sm + L.a2;
     const float *b1s = reinterpret_cast<const float *>(sm + L.b1);
-    const uint32_t TC = tcols_for(P.hidden);
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_addr(&tslot)), "r"(TC));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tslot)), "r"(WS_TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar_h)));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar_ld[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar_mm[i])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fail = 0;
     }
     if (P.hidden > 0) {
         copy16(W1s, P.W1p, P.hidden * P.K1 * 2, tid, TM);
         copy16(sm + L.b1, P.b1, P.hidden * 4, tid, TM);
     }
-    if (P.w2_resident) copy16(W2s, P.W2p, P.NOP * P.K2P * 2, tid, TM);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tbase = tslot;
     const uint32_t tl = tbase + ((uint32_t)(32 * warp) << 16);
-    uint32_t phase = 0;
-    bool aborted = false;
     const uint32_t sbo2 = (uint32_t)(P.K2P >> 3) * 128u;
+    const int nchunks = (P.NOP + P.nch - 1) / P.nch;
+    // phases (bit b for buffer b): bar_h and bar_mm are waited by every thread,
+    // bar_ld by thread 0; pending bits are thread 0's view
+    uint32_t ph_h = 0, ph_mm = 0, ph_ld = 0, ld_pending = 0, mm_pending = 0;
+    uint32_t mm_par = 0;   // thread 0: the parity each pending MMA's completion will have
+    bool aborted = false;
+    const auto w2buf = [&](int b) { return sm + (b ? L.w2b : L.w2a); };
+    const auto ldbar = [&](int b) { return smem_addr(b ? &bar_ld[1] : &bar_ld[0]); };
+    const auto mmbar = [&](int b) { return smem_addr(b ? &bar_mm[1] : &bar_mm[0]); };
+
+    // thread 0: the W2 rows of chunk c into buffer b
+    const auto copy_chunk = [&](int c, int b) {
+        const int o0 = c * P.nch, nw = min(P.nch, P.NOP - o0);
+        bulk_g2s(smem_addr(w2buf(b)), P.W2p + (size_t)o0 * P.K2P, (uint32_t)(nw * P.K2P * 2), ldbar(b));
+        ld_pending |= 1u << b;
+    };
+    // thread 0: wait for chunk c's W2 rows, then its MMA chain into accumulator b
+    const auto mma_chunk = [&](int c, int b) -> bool {
+        const bool ok = mbar_wait(ldbar(b), (ph_ld >> b) & 1u);
+        ph_ld ^= 1u << b;
+        ld_pending &= ~(1u << b);
+        if (!ok) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int nw = min(P.nch, P.NOP - c * P.nch);
+        const uint64_t da = umma_desc(smem_addr(A2), 128u, sbo2);
+        const uint64_t db = umma_desc(smem_addr(w2buf(b)), 128u, sbo2);
+        const uint32_t id = idesc_bf16(TM, nw);
+        for (int ks = 0; ks < (P.K2P >> 4); ++ks)
+            umma_bf16(tbase + (uint32_t)(b * P.nch), da + (uint64_t)(16 * ks), db + (uint64_t)(16 * ks), id,
+                      ks > 0 ? 1u : 0u);
+        umma_commit(mmbar(b));
+        mm_pending |= 1u << b;
+        mm_par = (mm_par & ~(1u << b)) | (ph_mm & (1u << b));
+        return true;
+    };
 
     for (int tile = blockIdx.x; tile < P.ntiles && !aborted; tile += gridDim.x) {
         const int c = tile * TM + tid;
         const bool valid = c < P.ncols;
         const int n = valid ? c / P.J : 0, j = valid ? c - n * P.J : 0;
+        // both W2 buffers are free here (every MMA of the previous tile was waited
+        // for): start the first two chunks' copies so they overlap the features
+        if (tid == 0) {
+            copy_chunk(0, 0);
+            if (nchunks > 1) copy_chunk(1, 1);
+        }
         // ---- features of this thread's column, bf16, into the f columns of A2 (row
         // tid); 32 loads in flight
         {
             float fv0 = 0.0f, fq0 = 0.0f;
             float inv_v = 0.0f;
             if (valid) {
-                const JointFeat jf = joint_feat(P.bnd, P.J, j, P.q0[j], P.v0[j]);
-                inv_v = (float)(1.0 / jf.vmax);
-                fv0 = (float)jf.fv0;
-                fq0 = (float)jf.fq0;
+                // FP32 feature constants (the predictor's inputs are rounded to bf16)
+                const float4 c4 = reinterpret_cast<const float4 *>(P.jf)[j];
+                inv_v = c4.x;
+                fv0 = P.v0[j] * c4.x;
+                fq0 = (P.q0[j] - c4.y) * c4.z;
             }
             const float *xs = P.xi + (size_t)n * P.H * P.J + j;
             for (int k0 = 0; k0 < P.K1; k0 += 32) {
@@ -474,20 +537,18 @@ __global__ void __launch_bounds__(TM, 4) ws_predict_kernel(const __grid_constant
         // ---- hidden layer: D[:, 0:hidden] = F W1^T (F: the f columns of A2, same
         // row-group stride), then h = max(0, D + b1) into the first columns of A2
         if (P.hidden > 0) {
-            if (warp == 0) {
-                if (elect_one()) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint64_t da = umma_desc(smem_addr(A2 + cm16(0, P.hidden, P.K2P)), 128u, sbo2);
-                    const uint64_t db = umma_desc(smem_addr(W1s), 128u, (uint32_t)(P.K1 >> 3) * 128u);
-                    const uint32_t id = idesc_bf16(TM, P.hidden);
-                    for (int ks = 0; ks < (P.K1 >> 4); ++ks)
-                        umma_bf16(tbase, da + (uint64_t)(16 * ks), db + (uint64_t)(16 * ks), id, ks > 0 ? 1u : 0u);
-                    umma_commit(smem_addr(&bar));
-                }
-                __syncwarp();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t da = umma_desc(smem_addr(A2 + cm16(0, P.hidden, P.K2P)), 128u, sbo2);
+                const uint64_t db = umma_desc(smem_addr(W1s), 128u, (uint32_t)(P.K1 >> 3) * 128u);
+                const uint32_t id = idesc_bf16(TM, P.hidden);
+                for (int ks = 0; ks < (P.K1 >> 4); ++ks)
+                    umma_bf16(tbase, da + (uint64_t)(16 * ks), db + (uint64_t)(16 * ks), id, ks > 0 ? 1u : 0u);
+                umma_commit(smem_addr(&bar_h));
             }
-            const bool ok = mbar_wait(smem_addr(&bar), phase);
-            phase ^= 1u;
+            __syncwarp();
+            const bool ok = mbar_wait(smem_addr(&bar_h), ph_h);
+            ph_h ^= 1u;
             if (__syncthreads_or(!ok)) {
                 aborted = true;
                 break;
@@ -517,46 +578,39 @@ __global__ void __launch_bounds__(TM, 4) ws_predict_kernel(const __grid_constant
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
         }
-        // ---- output layer in chunks of nch outputs: D[:, 0:nw] = A2 W2[o0 : o0 + nw]^T;
+        // ---- output layer: the first two chunks' MMAs (their accumulators overlap
+        // the hidden layer's columns, read back above)
+        if (tid == 0) {
+            bool ok = mma_chunk(0, 0);
+            if (ok && nchunks > 1) ok = mma_chunk(1, 1);
+            if (!ok) fail = 1;
+        }
         // output o of this column: dual_init[n][o][j] (o < D), x_init[n][o - D][j]
         float *const pd = P.dual_init + (size_t)n * P.D * P.J + j;
         float *const px = P.x_init + (size_t)n * P.H * P.J + j;
-        for (int o0 = 0; o0 < P.NOP; o0 += P.nch) {
-            const int nw = min(P.nch, P.NOP - o0);
-            unsigned char *W2c = W2s + (P.w2_resident ? (size_t)o0 * P.K2P * 2 : 0);
-            if (!P.w2_resident) {
-                copy16(W2s, P.W2p + (size_t)o0 * P.K2P, nw * P.K2P * 2, tid, TM);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncthreads();
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int b = ch & 1, o0 = ch * P.nch, nw = min(P.nch, P.NOP - o0);
+            const bool ok = mbar_wait(mmbar(b), (ph_mm >> b) & 1u);
+            ph_mm ^= 1u << b;
+            if (tid == 0) {
+                if (ok) mm_pending &= ~(1u << b);
+                // chunk ch's MMA has read its W2 buffer: fetch chunk ch + 2 into it
+                if (ok && ch + 2 < nchunks) copy_chunk(ch + 2, b);
             }
-            if (warp == 0) {
-                if (elect_one()) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint64_t da = umma_desc(smem_addr(A2), 128u, sbo2);
-                    const uint64_t db = umma_desc(smem_addr(W2c), 128u, sbo2);
-                    const uint32_t id = idesc_bf16(TM, nw);
-                    for (int ks = 0; ks < (P.K2P >> 4); ++ks)
-                        umma_bf16(tbase, da + (uint64_t)(16 * ks), db + (uint64_t)(16 * ks), id, ks > 0 ? 1u : 0u);
-                    umma_commit(smem_addr(&bar));
-                }
-                __syncwarp();
-            }
-            const bool ok = mbar_wait(smem_addr(&bar), phase);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
+            if (__syncthreads_or(!ok || fail)) {
                 aborted = true;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int g = 0; g < nw; g += 32) {
                 float v[32];
+                const uint32_t col = tl + (uint32_t)(b * P.nch + g);
                 if (g + 32 <= nw) {
-                    tmem_ld32(tl + (uint32_t)g, v);
+                    tmem_ld32(col, v);
                 } else {
 #pragma unroll
                     for (int q = 0; q < 32; q += 8)
-                        if (g + q < nw) tmem_ld8(tl + (uint32_t)(g + q), v + q);
+                        if (g + q < nw) tmem_ld8(col + (uint32_t)q, v + q);
                 }
                 if (valid) {
                     const int ob = o0 + g;
@@ -570,21 +624,25 @@ __global__ void __launch_bounds__(TM, 4) ws_predict_kernel(const __grid_constant
                     }
                 }
             }
-            // the tensor-memory reads are done before the next MMA overwrites D and
-            // before the next chunk of W2 overwrites its shared memory
+            // accumulator b has been read back: chunk ch + 2 may overwrite it
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
+            if (tid == 0 && ch + 2 < nchunks && !mma_chunk(ch + 2, b)) fail = 1;
         }
     }
-    if (aborted) {
-        if (tid == 0) {
-            if (P.err) atomicExch(P.err, 1);
-            (void)mbar_wait(smem_addr(&bar), phase ^ 1u);   // the last commit's MMAs, bounded
+    if (aborted && tid == 0) {
+        if (P.err) atomicExch(P.err, 1);
+        // copies and MMAs still in flight, each waited for (bounded) before the
+        // shared and tensor memory they write is released
+        for (int b = 0; b < 2; ++b) {
+            if ((ld_pending >> b) & 1u) (void)mbar_wait(ldbar(b), (ph_ld >> b) & 1u);
+            if ((mm_pending >> b) & 1u) (void)mbar_wait(mmbar(b), (mm_par >> b) & 1u);
         }
+        (void)mbar_wait(smem_addr(&bar_h), ph_h ^ 1u, 1u << 12);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(TC));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(WS_TCOLS));
 }
 
 prism_status check_ws(prism_ws_t w)
@@ -602,6 +660,7 @@ void free_ws(prism_ws_t w)
     cudaFree(w->d_W1);
     cudaFree(w->d_b1);
     cudaFree(w->d_b1f);
+    cudaFree(w->d_jf);
     cudaFree(w->d_W1p);
     cudaFree(w->d_W2p);
     cudaFree(w->d_G);
@@ -666,38 +725,52 @@ prism_status prism_ws_create(prism_proj_t h, int hidden, const double *W1_host, 
     const int static_smem = (int)fa.sharedSizeBytes;
     const int by_regs = 65536 / (std::max(fa.numRegs, 1) * TM);
     const auto per_sm_of = [&](int dyn) {
-        return std::min(std::min(smem_sm / (dyn + static_smem + reserved), by_regs),
-                        512 / (int)(hidden > NCH ? 256 : 128));
+        return std::min(std::min(smem_sm / (dyn + static_smem + reserved), by_regs), 512 / (int)WS_TCOLS);
     };
-    // the most resident blocks per SM; among equals W2 resident, then the widest chunk
+    // candidate chunk widths (two chunks' accumulators share the block's 128
+    // tensor-memory columns with the hidden layer); each call picks the one with
+    // the fewest waves for its batch, then the widest
     int best = 0;
-    const int chunks[] = {NCH, 96, 64, 48, 32, 16};
-    for (int res = 1; res >= 0; --res)
-        for (int nc : chunks) {
-            if (res && nc != NCH) continue;
-            const int tot = ws_smem(hidden, w->K1, w->K2P, w->NOP, res != 0, nc).total;
-            const int per = tot <= smem_blk ? per_sm_of(tot) : 0;
-            if (per > best) {
-                best = per;
-                w->w2_resident = res;
-                w->nch = nc;
-                w->smem = tot;
-            }
-        }
+    w->sms = sms;
+    for (int nc : {64, 48, 32, 16}) {
+        const int tot = ws_smem(hidden, w->K1, w->K2P, nc).total;
+        const int per = tot <= smem_blk ? per_sm_of(tot) : 0;
+        if (per < 1) continue;
+        w->cfg_nch[w->ncfg] = nc;
+        w->cfg_smem[w->ncfg] = tot;
+        w->cfg_per_sm[w->ncfg] = per;
+        ++w->ncfg;
+        if (tot > w->smem) w->smem = tot;
+        best = std::max(best, per);
+    }
     if (best < 1) {
         delete w;
         return wfail(PRISM_ERR_UNSUPPORTED, "predictor shared memory exceeds %d B", smem_blk);
     }
-    w->max_grid = best * sms;
+
     if ((st = ws_alloc(&w->d_W1, (size_t)hidden * w->d)) || (st = ws_alloc(&w->d_b1, hidden)) ||
         (st = ws_alloc(&w->d_b1f, hidden)) || (st = ws_alloc(&w->d_W1p, (size_t)std::max(hidden, 16) * w->K1)) ||
         (st = ws_alloc(&w->d_W2p, (size_t)w->NOP * w->K2P)) || (st = ws_alloc(&w->d_G, (size_t)w->K2 * w->ZW)) ||
         (st = ws_alloc(&w->d_M, (size_t)w->K2 * w->K2)) || (st = ws_alloc(&w->d_R, (size_t)w->K2 * w->NO)) ||
-        (st = ws_alloc(&w->d_W2, (size_t)w->K2 * w->NO)) || (st = ws_alloc(&w->d_flag, 1))) {
+        (st = ws_alloc(&w->d_W2, (size_t)w->K2 * w->NO)) || (st = ws_alloc(&w->d_flag, 1)) ||
+        (st = ws_alloc(&w->d_jf, (size_t)4 * J))) {
         free_ws(w);
         return st;
     }
-    if (hidden > 0) {
+    {
+        double bh[8 * PRISM_MAX_J];
+        float jf[4 * PRISM_MAX_J];
+        e = cudaMemcpy(bh, bnd, sizeof(double) * 8 * J, cudaMemcpyDeviceToHost);
+        for (int j = 0; j < J && e == cudaSuccess; ++j) {
+            const double qmin = bh[B_QMIN * J + j], qmax = bh[B_QMAX * J + j], vmax = bh[B_VMAX * J + j];
+            jf[4 * j] = (float)(1.0 / vmax);
+            jf[4 * j + 1] = (float)(0.5 * (qmin + qmax));
+            jf[4 * j + 2] = (float)(1.0 / (0.5 * (qmax - qmin)));
+            jf[4 * j + 3] = 0.0f;
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(w->d_jf, jf, sizeof(float) * 4 * J, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && hidden > 0) {
         float b1f[WS_MAX_HIDDEN];
         for (int i = 0; i < hidden; ++i) b1f[i] = (float)b1_host[i];
         e = cudaMemcpy(w->d_W1, W1_host, sizeof(double) * hidden * w->d, cudaMemcpyHostToDevice);
@@ -806,9 +879,21 @@ prism_status prism_ws_predict(prism_ws_t w, int batch, const float *q0, const fl
     p.K1 = w->K1;
     p.hidden = w->hidden;
     p.K2P = w->K2P;
-    p.w2_resident = w->w2_resident;
-    p.nch = w->nch;
     p.ntiles = (p.ncols + TM - 1) / TM;
+    // fewest waves of tiles, then the widest chunk
+    int pick = 0;
+    long long best_waves = -1;
+    for (int i = 0; i < w->ncfg; ++i) {
+        const long long slots = (long long)w->cfg_per_sm[i] * w->sms;
+        const long long waves = (p.ntiles + slots - 1) / slots;
+        if (best_waves < 0 || waves < best_waves) {
+            best_waves = waves;
+            pick = i;
+        }
+    }
+    p.nch = w->cfg_nch[pick];
+    const int smem_pick = w->cfg_smem[pick];
+    const int grid_pick = (int)std::min<long long>(p.ntiles, (long long)w->cfg_per_sm[pick] * w->sms);
     p.bnd = w->d_bounds;
     p.q0 = q0;
     p.v0 = v0;
@@ -816,11 +901,11 @@ prism_status prism_ws_predict(prism_ws_t w, int batch, const float *q0, const fl
     p.W1p = w->d_W1p;
     p.W2p = w->d_W2p;
     p.b1 = w->d_b1f;
+    p.jf = w->d_jf;
     p.x_init = x_init;
     p.dual_init = dual_init;
     p.err = prism_internal_err_flag(w->h);
-    const int grid = std::max(1, std::min(p.ntiles, w->max_grid));
-    ws_predict_kernel<<<grid, TM, w->smem, (cudaStream_t)cuda_stream>>>(p);
+    ws_predict_kernel<<<std::max(1, grid_pick), TM, smem_pick, (cudaStream_t)cuda_stream>>>(p);
     WS_CUDA(cudaGetLastError());
     return PRISM_OK;
 }
