@@ -635,8 +635,11 @@ def run_learned_ws(args):
     out = torch.empty_like(ins[0][0])
     pr = torch.empty((w.N, w.J), device=dev)
     du = torch.empty((w.N, w.J), device=dev)
-    xin = torch.empty_like(ins[0][0])
-    uin = torch.empty((w.N, 4 * w.H - 1, w.J), device=dev)
+    # the predictor writes, and the solve reads, the column-major warm-start layout
+    # ([H][N*J], [D][N*J]: whole 128-byte lines per warp)
+    CM = pp.INIT_COLUMN_MAJOR
+    xin = torch.empty((w.H, w.N * w.J), device=dev)
+    uin = torch.empty((4 * w.H - 1, w.N * w.J), device=dev)
     # ---- accuracy: cold at the workload's iteration count vs warm over a sweep
     n_acc = 4
     refs = [P.solve(q0, v0, xi, conv_iters, want_res=False)[0].clone() for (xi, q0, v0) in ins[:n_acc]]
@@ -657,8 +660,8 @@ def run_learned_ws(args):
 
     def warm_solve(iters):
         def f(xi, q0, v0):
-            model.predict(q0, v0, xi, x_init=xin, dual_init=uin)
-            P.solve_ex(q0, v0, xi, iters, x_init=xin, dual_init=uin, out=out, primal=pr, dual=du)
+            model.predict(q0, v0, xi, x_init=xin, dual_init=uin, layout=CM)
+            P.solve_ex(q0, v0, xi, iters, x_init=xin, dual_init=uin, out=out, primal=pr, dual=du, init_layout=CM)
             return out, pr
         return f
 
@@ -697,12 +700,13 @@ def run_learned_ws(args):
 
     def warm_step(k):
         xi, q0, v0 = ins[k % N_INPUTS]
-        model.predict(q0, v0, xi, x_init=xin, dual_init=uin)
-        P.solve_ex(q0, v0, xi, L_w or w.iters, x_init=xin, dual_init=uin, out=out, primal=pr, dual=du)
+        model.predict(q0, v0, xi, x_init=xin, dual_init=uin, layout=CM)
+        P.solve_ex(q0, v0, xi, L_w or w.iters, x_init=xin, dual_init=uin, out=out, primal=pr, dual=du,
+                   init_layout=CM)
 
     def pred_step(k):
         xi, q0, v0 = ins[k % N_INPUTS]
-        model.predict(q0, v0, xi, x_init=xin, dual_init=uin)
+        model.predict(q0, v0, xi, x_init=xin, dual_init=uin, layout=CM)
 
     def graph_timed(step):
         """Per-step ms of N_INPUTS consecutive steps captured in one CUDA graph and
@@ -776,7 +780,7 @@ def run_learned_ws(args):
             "data": "synthetic (seeded; no dataset)",
             "config": {"workload": f"learned warm start: realistic step (N={w.N}, J={w.J}, H={w.H}, dt={w.dt}), "
                                    f"warm-started solve at the accuracy of {w.iters} cold iterations",
-                       "hidden": args.ws_hidden, "lambda": args.ws_lambda,
+                       "hidden": args.ws_hidden, "lambda": args.ws_lambda, "init_layout": "column-major",
                        "train_columns": args.ws_train_steps * w.N * w.J, "train_iterations": conv_iters,
                        "l2": f"inputs larger than L2: {N_INPUTS} held-out steps cycled"},
             "iterations": {"cold": w.iters, "warm": L_w},

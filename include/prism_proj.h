@@ -157,17 +157,25 @@ prism_status prism_proj_solve(prism_proj_t h, int batch, const float *q0, const 
  *   dual_out  device float [N][D][J] multiplier after the last iteration, or NULL
  *   polish_iters  for PRISM_PREC_TF32: how many final iterations use the split
  *             (FP32-accurate) K-apply; ignored for other precisions
+ *   init_layout  PRISM_INIT_SAMPLE_MAJOR (0, the layouts above) or
+ *             PRISM_INIT_COLUMN_MAJOR (1): x_init [H][N*J] and dual_init
+ *             [D][N*J], column n*J + j contiguous (what prism_ws_predict writes
+ *             with coalesced stores); dual_out keeps [N][D][J]
  *   D = 4H-1 in ADMM mode: the multiplier of the row-normalised two-sided rows
  *   in the order velocity k=1..H, position k=1..H, acceleration k=1..H, jerk
  *   k=2..H (the scaled ADMM multiplier u of the oracle, same units under
  *   PRISM_SCALE_ROWNORM; under PRISM_SCALE_NONE the printed rows' units);
  *   D = H in PAPER mode: lambda of Eq. admm_dual.
  */
+#define PRISM_INIT_SAMPLE_MAJOR 0
+#define PRISM_INIT_COLUMN_MAJOR 1
+
 typedef struct {
     const float *x_init;
     const float *dual_init;
     float *dual_out;
     int polish_iters;
+    int init_layout;
 } prism_solve_opts;
 
 prism_status prism_proj_solve_ex(prism_proj_t h, int batch, const float *q0, const float *v0,
@@ -539,8 +547,10 @@ prism_status prism_ws_accumulate(prism_ws_t w, int batch, const float *q0, const
 prism_status prism_ws_fit(prism_ws_t w, double lambda, void *cuda_stream);
 
 /*
- * prism_ws_predict -- the fitted model on a batch: x_init device float
- * [N][H][J] and dual_init device float [N][D][J] for prism_proj_solve_ex.
+ * prism_ws_predict -- the fitted model on a batch: x_init and dual_init for
+ * prism_proj_solve_ex, in layout PRISM_INIT_SAMPLE_MAJOR (device float
+ * [N][H][J] and [N][D][J]) or PRISM_INIT_COLUMN_MAJOR ([H][N*J] and [D][N*J],
+ * whose stores are whole 128-byte lines; pass the same layout to the solve).
  * Runs on the tensor cores with bf16 operands and FP32 accumulation (the
  * prediction is a starting point, the solve sets the accuracy).  Enqueued on
  * cuda_stream; a bounded device-side wait that ran out raises the handle's
@@ -548,7 +558,7 @@ prism_status prism_ws_fit(prism_ws_t w, double lambda, void *cuda_stream);
  * PRISM_ERR_NOT_FACTORED.
  */
 prism_status prism_ws_predict(prism_ws_t w, int batch, const float *q0, const float *v0, const float *samples,
-                              float *x_init, float *dual_init, void *cuda_stream);
+                              float *x_init, float *dual_init, int layout, void *cuda_stream);
 
 /*
  * prism_ws_get -- synchronous copies for inspection: S = Phi^T Phi host double

@@ -391,6 +391,7 @@ struct SolveParams {
     int *err;                            // set to 1 if a tensor-core wait ran out
     const float *x_init;                 // [N][H][J] warm-start iterate or NULL (x^0 = xi)
     const float *dual_init;              // [N][D][J] warm-start multiplier or NULL (0)
+    int init_cm;                         // x_init / dual_init column-major: [H][N*J], [D][N*J]
     float *dual_out;                     // [N][D][J] final multiplier or NULL
     int polish;                          // tensor cores: last iterations with the split K-apply
     int D;                               // multiplier rows per column: 4H-1 (ADMM) or H (PAPER)
@@ -524,6 +525,33 @@ __device__ __forceinline__ void store_tile_cols(float *__restrict__ dst, const f
     for (; w.e < w.total; tile_walk_next(w, H, J, nth)) {
         const int cc = w.s * J + w.j - w.c_off;
         if ((unsigned)cc < (unsigned)Ct) base[w.e] = xs[(w.k + 2) * CP + cc];
+    }
+}
+
+// The tile's columns of a column-major [H][ncols] array (column C0 + cc at
+// offset k*ncols + C0 + cc) into slab rows k + 2; eight loads in flight per thread.
+__device__ __forceinline__ void load_tile_cols_cm(const float *__restrict__ src, long long ncols, float *xs, int CP,
+                                                  int C0, int Ct, int H, int tid, int nth)
+{
+    const int total = Ct * H;
+    constexpr int U = 8;
+    for (int e0 = tid; e0 < total; e0 += U * nth) {
+        float v[U];
+        int at[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * nth;
+            at[u] = -1;
+            v[u] = 0.0f;
+            if (e < total) {
+                const int k = e / Ct, cc = e - k * Ct;
+                v[u] = __ldg(src + (size_t)k * ncols + C0 + cc);
+                at[u] = (k + 2) * CP + cc;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (at[u] >= 0) xs[at[u]] = v[u];
     }
 }
 
@@ -1048,6 +1076,8 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                     if (p.xi_out) p.xi_out[e] = v;
                 }
             }
+        } else if (p.x_init && p.init_cm) {
+            load_tile_cols_cm(p.x_init, (long long)p.N * J, xs, CP, n0 * J, Tt * J, H, tid, NTHREADS);
         } else {
             const float *src = (p.x_init ? p.x_init : p.xi) + (size_t)n0 * HJ;
             const int total = Tt * HJ;
@@ -1108,21 +1138,22 @@ solve_kernel(const __grid_constant__ LaunchParams P)
             if (p.dual_init && colv) {
                 // warm-start multiplier: u' (scaled rows, the oracle's units) -> u = u'/sqrt(w)
                 // in the device units, t = y - u.  PAPER mode: lambda as is.
-                const size_t base = (size_t)(n0 + nl_c) * p.D * J + jj;
+                const size_t base = p.init_cm ? (size_t)(n0 + nl_c) * J + jj : (size_t)(n0 + nl_c) * p.D * J + jj;
+                const size_t rs = p.init_cm ? (size_t)p.N * J : (size_t)J;   // between rows
 #pragma unroll
                 for (int r = 0; r < HQ; ++r) {
                     const int i = i0 + r;
                     if (i < H) {
                         if (MODE == PRISM_MODE_ADMM) {
-                            t_v[r] -= __ldg(p.dual_init + base + (size_t)i * J) * rsqrtf(wv);
-                            t_p[r] -= __ldg(p.dual_init + base + (size_t)(H + i) * J) * rsqrtf(wps[i]);
-                            t_a[r] -= __ldg(p.dual_init + base + (size_t)(2 * H + i) * J) *
+                            t_v[r] -= __ldg(p.dual_init + base + (size_t)i * rs) * rsqrtf(wv);
+                            t_p[r] -= __ldg(p.dual_init + base + (size_t)(H + i) * rs) * rsqrtf(wps[i]);
+                            t_a[r] -= __ldg(p.dual_init + base + (size_t)(2 * H + i) * rs) *
                                       rsqrtf(i == 0 ? wa0 : wa);
                             if (i >= 1)
-                                t_j[r] -= __ldg(p.dual_init + base + (size_t)(3 * H + i - 1) * J) *
+                                t_j[r] -= __ldg(p.dual_init + base + (size_t)(3 * H + i - 1) * rs) *
                                           rsqrtf(i == 1 ? wj0 : wj);
                         } else {
-                            lam[r] = __ldg(p.dual_init + base + (size_t)i * J);
+                            lam[r] = __ldg(p.dual_init + base + (size_t)i * rs);
                         }
                     }
                 }
@@ -1769,7 +1800,10 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
                 }
             }
         } else {
-            load_tile_cols(p.x_init ? p.x_init : p.xi, xs, CP, C0, Ct, H, J, tid, NTH);
+            if (p.x_init && p.init_cm)
+                load_tile_cols_cm(p.x_init, (long long)p.N * J, xs, CP, C0, Ct, H, tid, NTH);
+            else
+                load_tile_cols(p.x_init ? p.x_init : p.xi, xs, CP, C0, Ct, H, J, tid, NTH);
         }
         __syncthreads();
         // ---- a2: bounds, x^0 (x_0 := v0), the halo and the prefix over earlier quarters
@@ -1825,14 +1859,15 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
         }
         // ---- u^0 of row i of kind k (0 velocity, 1 position, 2 acceleration, 3 jerk) in the
         // device units: the warm-start multiplier u' (the oracle's units, unit rows) / sqrt(w)
-        const size_t dbase = (size_t)n_c * p.D * J + jj;
+        const size_t dbase = p.init_cm ? (size_t)(C0 + c) : (size_t)n_c * p.D * J + jj;
+        const size_t drs = p.init_cm ? (size_t)p.N * J : (size_t)J;   // between multiplier rows
         const auto u0 = [&](int kind, int i) -> float {
             if (!p.dual_init || !colv || i >= H) return 0.0f;
-            if (kind == 0) return __ldg(p.dual_init + dbase + (size_t)i * J) * rsqrtf(p.wv);
-            if (kind == 1) return __ldg(p.dual_init + dbase + (size_t)(H + i) * J) * rsqrtf(p.wp[i]);
-            if (kind == 2) return __ldg(p.dual_init + dbase + (size_t)(2 * H + i) * J) * rsqrtf(i == 0 ? p.wa0 : p.wa);
+            if (kind == 0) return __ldg(p.dual_init + dbase + (size_t)i * drs) * rsqrtf(p.wv);
+            if (kind == 1) return __ldg(p.dual_init + dbase + (size_t)(H + i) * drs) * rsqrtf(p.wp[i]);
+            if (kind == 2) return __ldg(p.dual_init + dbase + (size_t)(2 * H + i) * drs) * rsqrtf(i == 0 ? p.wa0 : p.wa);
             if (i < 1) return 0.0f;
-            return __ldg(p.dual_init + dbase + (size_t)(3 * H + i - 1) * J) * rsqrtf(i == 1 ? p.wj0 : p.wj);
+            return __ldg(p.dual_init + dbase + (size_t)(3 * H + i - 1) * drs) * rsqrtf(i == 1 ? p.wj0 : p.wj);
         };
         // ---- initial multiplier state m = u^0 - y^0 (0 on rows that do not exist)
         float2 Mv[NP], Mp[NP], Ma[NP], Mj[NP];
@@ -2290,7 +2325,10 @@ solve_kernel_q8(const __grid_constant__ LaunchParams P)
                 }
             }
         } else {
-            load_tile_cols(p.x_init ? p.x_init : p.xi, xs, CP, C0, Ct, H, J, tid, NTH);
+            if (p.x_init && p.init_cm)
+                load_tile_cols_cm(p.x_init, (long long)p.N * J, xs, CP, C0, Ct, H, tid, NTH);
+            else
+                load_tile_cols(p.x_init ? p.x_init : p.xi, xs, CP, C0, Ct, H, J, tid, NTH);
         }
         __syncthreads();
         // ---- a2: bounds, x^0 (x_0 := v0), the halo and the sum over earlier quarters
@@ -2346,14 +2384,15 @@ solve_kernel_q8(const __grid_constant__ LaunchParams P)
             rowof(Ya, HQ) = 0.0f;
             rowof(Yj, HQ) = 0.0f;
         };
-        const size_t dbase = (size_t)n_c * p.D * J + jj;
+        const size_t dbase = p.init_cm ? (size_t)(C0 + c) : (size_t)n_c * p.D * J + jj;
+        const size_t drs = p.init_cm ? (size_t)p.N * J : (size_t)J;   // between multiplier rows
         const auto u0 = [&](int kind, int i) -> float {
             if (!p.dual_init || !colv || i >= H) return 0.0f;
-            if (kind == 0) return __ldg(p.dual_init + dbase + (size_t)i * J) * rsqrtf(p.wv);
-            if (kind == 1) return __ldg(p.dual_init + dbase + (size_t)(H + i) * J) * rsqrtf(p.wp[i]);
-            if (kind == 2) return __ldg(p.dual_init + dbase + (size_t)(2 * H + i) * J) * rsqrtf(i == 0 ? p.wa0 : p.wa);
+            if (kind == 0) return __ldg(p.dual_init + dbase + (size_t)i * drs) * rsqrtf(p.wv);
+            if (kind == 1) return __ldg(p.dual_init + dbase + (size_t)(H + i) * drs) * rsqrtf(p.wp[i]);
+            if (kind == 2) return __ldg(p.dual_init + dbase + (size_t)(2 * H + i) * drs) * rsqrtf(i == 0 ? p.wa0 : p.wa);
             if (i < 1) return 0.0f;
-            return __ldg(p.dual_init + dbase + (size_t)(3 * H + i - 1) * J) * rsqrtf(i == 1 ? p.wj0 : p.wj);
+            return __ldg(p.dual_init + dbase + (size_t)(3 * H + i - 1) * drs) * rsqrtf(i == 1 ? p.wj0 : p.wj);
         };
         float2 Mv[NP], Mp[NP], Ma[NP], Mj[NP];
         {
@@ -2944,7 +2983,7 @@ prism_status prepare_solve(prism_proj_t h, int batch, const float *q0, const flo
     p.Khi = h->d_Khi; p.Klo = h->d_Klo; p.err = h->d_err;
     p.Khi8 = h->d_Khi8; p.Klo8 = h->d_Klo8;
     p.Bz = h->d_Bz; p.Wz = h->d_Wz;
-    p.x_init = nullptr; p.dual_init = nullptr; p.dual_out = nullptr;
+    p.x_init = nullptr; p.dual_init = nullptr; p.dual_out = nullptr; p.init_cm = 0;
     p.D = (h->mode == PRISM_MODE_ADMM) ? 4 * h->H - 1 : h->H;
     p.tile0 = 0;
     p.s_mean = nullptr; p.s_std = nullptr; p.seed = 0; p.sstream = 0; p.xi_out = nullptr;
@@ -3389,6 +3428,9 @@ prism_status prism_proj_solve_ex(prism_proj_t h, int batch, const float *q0, con
         p.x_init = opts->x_init;
         p.dual_init = opts->dual_init;
         p.dual_out = opts->dual_out;
+        if (opts->init_layout != PRISM_INIT_SAMPLE_MAJOR && opts->init_layout != PRISM_INIT_COLUMN_MAJOR)
+            return fail(PRISM_ERR_INVALID_ARG, "bad init_layout %d", opts->init_layout);
+        p.init_cm = opts->init_layout == PRISM_INIT_COLUMN_MAJOR;
         if (h->prec == PRISM_PREC_TF32) p.polish = std::min(opts->polish_iters, iters);
         if (batch > 0 && opts->x_init && (const void *)opts->x_init == (const void *)out)
             return fail(PRISM_ERR_INVALID_ARG, "x_init must not alias out");
@@ -3728,6 +3770,7 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
         all[k].dual = q.dual_res;
         all[k].x_init = q.x_init;
         all[k].dual_init = q.dual_init;
+        all[k].init_cm = 0;
         all[k].dual_out = q.dual_out;
         pl->num_sms = q.h->num_sms;
         use_tc[k] = q.h->prec == PRISM_PREC_TF32X3 || q.h->prec == PRISM_PREC_TF32;

@@ -226,6 +226,7 @@ bool Server::enqueue(const std::shared_ptr<Request> &r, const Controller &c, boo
         o.dual_init = warm_in ? d_state : nullptr;
         o.dual_out = c.warm ? d_state : nullptr;
         o.polish_iters = 0;
+        o.init_layout = PRISM_INIT_SAMPLE_MAJOR;
         if (ok)
             ok = prism_proj_solve_ex(c.h, c.N, d_q0, d_v0, d_xi, c.iters, c.rho, &o, d_out, d_pr, nullptr, s) ==
                  PRISM_OK;

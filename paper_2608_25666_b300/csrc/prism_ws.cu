@@ -344,6 +344,7 @@ __global__ void ws_pack_kernel(const double *__restrict__ src, int rows, int col
 // ---------------------------------------------------------------------------
 struct WsPredictParams {
     int ncols, J, H, D, NO, NOP, d, K1, hidden, K2P, ntiles, nch;
+    int cm;                // outputs column-major ([D][ncols], [H][ncols]) instead of [N][D][J], [N][H][J]
     const double *bnd;
     const float *q0, *v0, *xi;
     const uint16_t *W1p, *W2p;
@@ -506,20 +507,18 @@ __global__ void __launch_bounds__(TM, 4) ws_predict_kernel(const __grid_constant
                 fv0 = P.v0[j] * c4.x;
                 fq0 = (P.q0[j] - c4.y) * c4.z;
             }
-            const float *xs = P.xi + (size_t)n * P.H * P.J + j;
+            const float *xs = P.xi + (size_t)n * P.H * P.J + j;   // a valid address for every thread
             for (int k0 = 0; k0 < P.K1; k0 += 32) {
                 float f[32];
+                // unconditional loads (steps past H re-read step H-1) so that all 32 are
+                // in flight together; the selection follows
+#pragma unroll
+                for (int i = 0; i < 32; ++i) f[i] = __ldg(xs + (size_t)min(k0 + i, P.H - 1) * P.J);
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int k = k0 + i;
-                    float v = 0.0f;
-                    if (valid) {
-                        if (k < P.H) v = __ldg(xs + (size_t)k * P.J) * inv_v;
-                        else if (k == P.H) v = fv0;
-                        else if (k == P.H + 1) v = fq0;
-                        else if (k == P.H + 2) v = 1.0f;
-                    }
-                    f[i] = v;
+                    float v = k < P.H ? f[i] * inv_v : k == P.H ? fv0 : k == P.H + 1 ? fq0 : k == P.H + 2 ? 1.0f : 0.0f;
+                    f[i] = valid ? v : 0.0f;
                 }
 #pragma unroll
                 for (int g = 0; g < 32; g += 8) {
@@ -585,9 +584,11 @@ __global__ void __launch_bounds__(TM, 4) ws_predict_kernel(const __grid_constant
             if (ok && nchunks > 1) ok = mma_chunk(1, 1);
             if (!ok) fail = 1;
         }
-        // output o of this column: dual_init[n][o][j] (o < D), x_init[n][o - D][j]
-        float *const pd = P.dual_init + (size_t)n * P.D * P.J + j;
-        float *const px = P.x_init + (size_t)n * P.H * P.J + j;
+        // output o of this column: dual_init[n][o][j] (o < D), x_init[n][o - D][j], or
+        // column-major dual_init[o][c], x_init[o - D][c] (a warp's stores: 128 bytes)
+        float *const pd = P.cm ? P.dual_init + c : P.dual_init + (size_t)n * P.D * P.J + j;
+        float *const px = P.cm ? P.x_init + c : P.x_init + (size_t)n * P.H * P.J + j;
+        const long long ostride = P.cm ? (long long)P.ncols : (long long)P.J;
         for (int ch = 0; ch < nchunks; ++ch) {
             const int b = ch & 1, o0 = ch * P.nch, nw = min(P.nch, P.NOP - o0);
             const bool ok = mbar_wait(mmbar(b), (ph_mm >> b) & 1u);
@@ -619,8 +620,8 @@ __global__ void __launch_bounds__(TM, 4) ws_predict_kernel(const __grid_constant
                     // (od <= 0 once ob >= D; ob + i - D >= 0 whenever i >= od)
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
-                        if (i < od) pd[(long long)(ob + i) * P.J] = v[i];
-                        else if (i < oe) px[(long long)(ob + i - P.D) * P.J] = v[i];
+                        if (i < od) pd[(long long)(ob + i) * ostride] = v[i];
+                        else if (i < oe) px[(long long)(ob + i - P.D) * ostride] = v[i];
                     }
                 }
             }
@@ -859,10 +860,12 @@ prism_status prism_ws_fit(prism_ws_t w, double lambda, void *cuda_stream)
 }
 
 prism_status prism_ws_predict(prism_ws_t w, int batch, const float *q0, const float *v0, const float *samples,
-                              float *x_init, float *dual_init, void *cuda_stream)
+                              float *x_init, float *dual_init, int layout, void *cuda_stream)
 {
     prism_status st = check_ws(w);
     if (st) return st;
+    if (layout != PRISM_INIT_SAMPLE_MAJOR && layout != PRISM_INIT_COLUMN_MAJOR)
+        return wfail(PRISM_ERR_INVALID_ARG, "bad layout %d", layout);
     if (!w->fitted) return wfail(PRISM_ERR_NOT_FACTORED, "prism_ws_fit has not succeeded");
     if (batch < 0) return wfail(PRISM_ERR_INVALID_ARG, "batch < 0");
     if (batch == 0) return PRISM_OK;
@@ -902,6 +905,7 @@ prism_status prism_ws_predict(prism_ws_t w, int batch, const float *q0, const fl
     p.W2p = w->d_W2p;
     p.b1 = w->d_b1f;
     p.jf = w->d_jf;
+    p.cm = layout == PRISM_INIT_COLUMN_MAJOR;
     p.x_init = x_init;
     p.dual_init = dual_init;
     p.err = prism_internal_err_flag(w->h);

@@ -33,10 +33,13 @@ _lock = threading.Lock()
 _lib = None
 
 
+INIT_SAMPLE_MAJOR, INIT_COLUMN_MAJOR = 0, 1   # warm-start input layouts of prism_proj_solve_ex
+
+
 class SolveOpts(ctypes.Structure):
     """prism_solve_opts of the C ABI."""
     _fields_ = [("x_init", ctypes.c_void_p), ("dual_init", ctypes.c_void_p),
-                ("dual_out", ctypes.c_void_p), ("polish_iters", ctypes.c_int)]
+                ("dual_out", ctypes.c_void_p), ("polish_iters", ctypes.c_int), ("init_layout", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -121,7 +124,7 @@ def lib() -> ctypes.CDLL:
             L.prism_ws_create.argtypes = [P, i, P, P, ctypes.POINTER(P)]
             L.prism_ws_accumulate.argtypes = [P, i, P, P, P, P, P, P]
             L.prism_ws_fit.argtypes = [P, d, P]
-            L.prism_ws_predict.argtypes = [P, i, P, P, P, P, P, P]
+            L.prism_ws_predict.argtypes = [P, i, P, P, P, P, P, i, P]
             L.prism_ws_get.argtypes = [P, P, P, P, ctypes.POINTER(ll)]
             L.prism_ws_reset.argtypes = [P]
             L.prism_ws_destroy.argtypes = [P]
@@ -228,22 +231,25 @@ class Projector:
 
     def solve_ex(self, q0, v0, samples, iters: int, rho: float | None = None, x_init=None,
                  dual_init=None, dual_out=None, polish_iters: int = 0, out=None, primal=None,
-                 dual=None, stream=None, want_res: bool = True, want_dual_out: bool = False):
-        """prism_proj_solve_ex: warm start (x_init, dual_init) and multiplier export."""
+                 dual=None, stream=None, want_res: bool = True, want_dual_out: bool = False,
+                 init_layout: int = 0):
+        """prism_proj_solve_ex: warm start (x_init, dual_init) and multiplier export.
+        init_layout INIT_COLUMN_MAJOR takes x_init [H][N*J] and dual_init [D][N*J]."""
         import torch
         N = int(samples.shape[0])
         D = self.dual_rows()
+        cm = init_layout == INIT_COLUMN_MAJOR
         if x_init is not None:
-            _need_cuda_f32("x_init", x_init, (N, self.H, self.J))
+            _need_cuda_f32("x_init", x_init, (self.H, N * self.J) if cm else (N, self.H, self.J))
         if dual_init is not None:
-            _need_cuda_f32("dual_init", dual_init, (N, D, self.J))
+            _need_cuda_f32("dual_init", dual_init, (D, N * self.J) if cm else (N, D, self.J))
         if want_dual_out and dual_out is None:
             dual_out = torch.empty((N, D, self.J), dtype=torch.float32, device=samples.device)
         if dual_out is not None:
             _need_cuda_f32("dual_out", dual_out, (N, D, self.J))
         opts = SolveOpts(None if x_init is None else x_init.data_ptr(),
                          None if dual_init is None else dual_init.data_ptr(),
-                         None if dual_out is None else dual_out.data_ptr(), int(polish_iters))
+                         None if dual_out is None else dual_out.data_ptr(), int(polish_iters), int(init_layout))
         L = lib()
 
         def fn(h, n, a, b_, c, it, r, o, pr, du, st):
@@ -530,21 +536,27 @@ class WarmStart:
         _check(lib().prism_ws_fit(self._h, float(lam), _stream_ptr(stream)))
         return self
 
-    def predict(self, q0, v0, samples, x_init=None, dual_init=None, stream=None):
-        """(x_init [N][H][J], dual_init [N][D][J]) on the device."""
+    def predict(self, q0, v0, samples, x_init=None, dual_init=None, layout: int = INIT_SAMPLE_MAJOR,
+                stream=None):
+        """(x_init, dual_init) on the device: [N][H][J] and [N][D][J], or with
+        layout INIT_COLUMN_MAJOR [H][N*J] and [D][N*J] (pass the same layout to
+        Projector.solve_ex)."""
         import torch
         N = int(samples.shape[0])
         _need_cuda_f32("q0", q0, (self.J,))
         _need_cuda_f32("v0", v0, (self.J,))
         _need_cuda_f32("samples", samples, (N, self.H, self.J))
+        cm = layout == INIT_COLUMN_MAJOR
+        xs = (self.H, N * self.J) if cm else (N, self.H, self.J)
+        us = (self.D, N * self.J) if cm else (N, self.D, self.J)
         if x_init is None:
-            x_init = torch.empty((N, self.H, self.J), dtype=torch.float32, device=samples.device)
+            x_init = torch.empty(xs, dtype=torch.float32, device=samples.device)
         if dual_init is None:
-            dual_init = torch.empty((N, self.D, self.J), dtype=torch.float32, device=samples.device)
-        _need_cuda_f32("x_init", x_init, (N, self.H, self.J))
-        _need_cuda_f32("dual_init", dual_init, (N, self.D, self.J))
+            dual_init = torch.empty(us, dtype=torch.float32, device=samples.device)
+        _need_cuda_f32("x_init", x_init, xs)
+        _need_cuda_f32("dual_init", dual_init, us)
         _check(lib().prism_ws_predict(self._h, N, _ptr(q0), _ptr(v0), _ptr(samples), _ptr(x_init),
-                                      _ptr(dual_init), _stream_ptr(stream)))
+                                      _ptr(dual_init), int(layout), _stream_ptr(stream)))
         return x_init, dual_init
 
     def get(self, want_w2: bool = True):

@@ -211,3 +211,38 @@ def test_errors():
     assert e.value.status == 2
     for p_ in (P, Pp, Pu):
         p_.close()
+
+
+@pytest.mark.parametrize("prec", [pp.PREC_TF32X3, pp.PREC_FP32], ids=["tc", "simt"])
+def test_column_major_layout_equals_sample_major(prec):
+    """The predictor's column-major outputs ([H][N*J], [D][N*J]) are its
+    sample-major outputs transposed, bit for bit, and a solve warm-started from
+    either layout gives identical results (ragged tiles: N*J = 444)."""
+    import torch
+    J, H, N, dt = 12, 50, 37, 0.02
+    b = workloads.make_custom(61, N, J, H, dt, offset_sigma=0.5)
+    D = 4 * H - 1
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(N, H, J)).astype(np.float32)
+    u = (0.1 * rng.normal(size=(N, D, J))).astype(np.float32)
+    W1, b1 = first_layer(32, H + 3, 8)
+    P = pp.Projector(J, H, dt, b["bounds"]).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, prec)
+    ws = pp.WarmStart(P, 32, W1=W1, b1=b1)
+    xi, q0, v0, xs, us = dev(b["xi"], b["q0"], b["v0"], x, u)
+    ws.accumulate(q0, v0, xi, xs, us).fit(0.1)
+    xs_, us_ = ws.predict(q0, v0, xi)
+    xc, uc = ws.predict(q0, v0, xi, layout=pp.INIT_COLUMN_MAJOR)
+    torch.cuda.synchronize()
+    assert tuple(xc.shape) == (H, N * J) and tuple(uc.shape) == (D, N * J)
+    assert torch.equal(xc, xs_.permute(1, 0, 2).reshape(H, N * J))
+    assert torch.equal(uc, us_.permute(1, 0, 2).reshape(D, N * J))
+    a = P.solve_ex(q0, v0, xi, 15, x_init=xs_, dual_init=us_, want_dual_out=True)
+    c = P.solve_ex(q0, v0, xi, 15, x_init=xc, dual_init=uc, want_dual_out=True, init_layout=pp.INIT_COLUMN_MAJOR)
+    torch.cuda.synchronize()
+    for ta, tc in zip(a, c):
+        assert torch.equal(ta, tc)
+    with pytest.raises(pp.PrismError) as e:
+        P.solve_ex(q0, v0, xi, 15, x_init=xs_, dual_init=us_, init_layout=2)
+    assert e.value.status == 1
+    ws.close()
+    P.close()
