@@ -1672,9 +1672,12 @@ __host__ __device__ constexpr int z_min_blocks() { return NW == 8 ? solve_min_bl
 // K slot, which meets the columns C of [K' | kb' | C].  (Carrying x^l as the
 // base instead of xi, which the x-step's optimality condition allows in exact
 // arithmetic, lets the rounding of each K-apply shift the problem being solved:
-// measured 2.3e-4 against the oracle after 100 iterations.)
+// measured 2.3e-4 against the oracle after 100 iterations.)  WARM: the
+// instantiation that reads warm-start inputs (x_init, dual_init, either
+// layout); solves without them run the other one, which has none of that code
+// (fewer registers).
 // ===========================================================================
-template <int HQ, int NW, bool BATCHED>
+template <int HQ, int NW, bool BATCHED, bool WARM>
 __global__ void __launch_bounds__(32 * NW, (z_min_blocks<HQ, NW>()))
 solve_kernel_z(const __grid_constant__ LaunchParams P)
 {
@@ -1800,10 +1803,10 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
                 }
             }
         } else {
-            if (p.x_init && p.init_cm)
+            if (WARM && p.x_init && p.init_cm)
                 load_tile_cols_cm(p.x_init, (long long)p.N * J, xs, CP, C0, Ct, H, tid, NTH);
             else
-                load_tile_cols(p.x_init ? p.x_init : p.xi, xs, CP, C0, Ct, H, J, tid, NTH);
+                load_tile_cols(WARM && p.x_init ? p.x_init : p.xi, xs, CP, C0, Ct, H, J, tid, NTH);
         }
         __syncthreads();
         // ---- a2: bounds, x^0 (x_0 := v0), the halo and the prefix over earlier quarters
@@ -1847,43 +1850,98 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
             rowof(Ya, HQ) = 0.0f;
             rowof(Yj, HQ) = 0.0f;
         };
-        // ---- xi of this thread's rows (the slab holds x_init instead when one is given)
-        {
-            const float *xisrc = p.xi + (size_t)n_c * HJ + jj;
+        // ---- xi of this thread's rows: from the slab, or (WARM with x_init, which the slab
+        // then holds) from global memory, unconditional loads at clamped steps so that
+        // they are in flight together
+        if constexpr (WARM) {
+            if (p.x_init) {
+                const float *xisrc = p.xi + (size_t)n_c * HJ + jj;   // a valid address for every thread
+                float v[2 * NP];
 #pragma unroll
-            for (int r = 0; r < 2 * NP; ++r) {
-                float v = 0.0f;
-                if (r < HQ && colv && i0 + r < H) v = p.x_init ? __ldg(xisrc + (size_t)(i0 + r) * J) : xs[(i0 + r + 2) * CP + c];
-                xit[r] = v;
+                for (int r = 0; r < 2 * NP; ++r) v[r] = __ldg(xisrc + (size_t)min(i0 + r, H - 1) * J);
+#pragma unroll
+                for (int r = 0; r < 2 * NP; ++r) xit[r] = (r < HQ && colv && i0 + r < H) ? v[r] : 0.0f;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 2 * NP; ++r)
+                    xit[r] = (r < HQ && colv && i0 + r < H) ? xs[(i0 + r + 2) * CP + c] : 0.0f;
             }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 2 * NP; ++r)
+                xit[r] = (r < HQ && colv && i0 + r < H) ? xs[(i0 + r + 2) * CP + c] : 0.0f;
         }
-        // ---- u^0 of row i of kind k (0 velocity, 1 position, 2 acceleration, 3 jerk) in the
-        // device units: the warm-start multiplier u' (the oracle's units, unit rows) / sqrt(w)
-        const size_t dbase = p.init_cm ? (size_t)(C0 + c) : (size_t)n_c * p.D * J + jj;
-        const size_t drs = p.init_cm ? (size_t)p.N * J : (size_t)J;   // between multiplier rows
-        const auto u0 = [&](int kind, int i) -> float {
-            if (!p.dual_init || !colv || i >= H) return 0.0f;
-            if (kind == 0) return __ldg(p.dual_init + dbase + (size_t)i * drs) * rsqrtf(p.wv);
-            if (kind == 1) return __ldg(p.dual_init + dbase + (size_t)(H + i) * drs) * rsqrtf(p.wp[i]);
-            if (kind == 2) return __ldg(p.dual_init + dbase + (size_t)(2 * H + i) * drs) * rsqrtf(i == 0 ? p.wa0 : p.wa);
-            if (i < 1) return 0.0f;
-            return __ldg(p.dual_init + dbase + (size_t)(3 * H + i - 1) * drs) * rsqrtf(i == 1 ? p.wj0 : p.wj);
-        };
-        // ---- initial multiplier state m = u^0 - y^0 (0 on rows that do not exist)
         float2 Mv[NP], Mp[NP], Ma[NP], Mj[NP];
-        {
+        if constexpr (!WARM) {
+            // ---- initial multiplier state m = u^0 - y^0 = -y^0 (0 on rows that do not exist):
+            // this instantiation takes no warm-start inputs (the dispatch sends solves with
+            // x_init or dual_init to the WARM one)
             float2 Yp[NP], Ya[NP], Yj[NP];
             rows_y(Yp, Ya, Yj);
 #pragma unroll
             for (int r = 0; r < HQ; ++r) {
                 const int i = i0 + r;
                 const bool vi = colv && i < H;
-                rowof(Mv, r) = vi ? u0(0, i) - rowof(X, r) : 0.0f;
-                rowof(Mp, r) = vi ? u0(1, i) - rowof(Yp, r) : 0.0f;
-                rowof(Ma, r) = vi ? u0(2, i) - rowof(Ya, r) : 0.0f;
-                rowof(Mj, r) = (vi && i >= 1) ? u0(3, i) - rowof(Yj, r) : 0.0f;
+                rowof(Mv, r) = vi ? 0.0f - rowof(X, r) : 0.0f;
+                rowof(Mp, r) = vi ? 0.0f - rowof(Yp, r) : 0.0f;
+                rowof(Ma, r) = vi ? 0.0f - rowof(Ya, r) : 0.0f;
+                rowof(Mj, r) = (vi && i >= 1) ? 0.0f - rowof(Yj, r) : 0.0f;
             }
             rowof(Mv, HQ) = rowof(Mp, HQ) = rowof(Ma, HQ) = rowof(Mj, HQ) = 0.0f;
+        } else {
+            // ---- initial multiplier state m = u^0 - y^0 (0 on rows that do not exist); u^0 = 0
+            // without dual_init.  With it, the multiplier u' (the oracle's units, unit
+            // rows) of row i of each kind (velocity, position, acceleration, jerk) is loaded
+            // unconditionally (clamped row, a valid address for every thread) so that the
+            // loads are in flight together, then scaled to the device units u = u' / sqrt(w)
+            // with the weight table
+#pragma unroll
+            for (int k = 0; k < NP; ++k) Mv[k] = Mp[k] = Ma[k] = Mj[k] = make_float2(0.0f, 0.0f);
+            if (WARM && p.dual_init) {
+                const size_t dbase = !colv ? 0 : p.init_cm ? (size_t)(C0 + c) : (size_t)n_c * p.D * J + jj;
+                const size_t drs = p.init_cm ? (size_t)p.N * J : (size_t)J;   // between multiplier rows
+                const float *ud = p.dual_init + dbase;
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = min(i0 + r, H - 1);
+                    rowof(Mv, r) = __ldg(ud + (size_t)i * drs);
+                    rowof(Mp, r) = __ldg(ud + (size_t)(H + i) * drs);
+                    rowof(Ma, r) = __ldg(ud + (size_t)(2 * H + i) * drs);
+                    rowof(Mj, r) = __ldg(ud + (size_t)(3 * H + max(i, 1) - 1) * drs);
+                }
+                const float rwv = rsqrtf(p.wv);
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    const bool vi = colv && i < H;
+                    const float2 wpp = wtab[b * NP + (r >> 1)], wap = wtab[(4 + b) * NP + (r >> 1)],
+                                 wjp = wtab[(8 + b) * NP + (r >> 1)];
+                    rowof(Mv, r) = vi ? rowof(Mv, r) * rwv : 0.0f;
+                    rowof(Mp, r) = vi ? rowof(Mp, r) * rsqrtf((r & 1) ? wpp.y : wpp.x) : 0.0f;
+                    rowof(Ma, r) = vi ? rowof(Ma, r) * rsqrtf((r & 1) ? wap.y : wap.x) : 0.0f;
+                    rowof(Mj, r) = (vi && i >= 1) ? rowof(Mj, r) * rsqrtf((r & 1) ? wjp.y : wjp.x) : 0.0f;
+                }
+            }
+            {
+                // m = u^0 - y^0, y = Fh x formed row by row as rows_y does
+                float cs = rowof(X, HQ), xm1 = h1, am1 = h1 - h0;
+#pragma unroll
+                for (int r = 0; r < HQ; ++r) {
+                    const int i = i0 + r;
+                    const bool vi = colv && i < H;
+                    const float xr = rowof(X, r);
+                    cs += xr;
+                    const float ya = xr - xm1;
+                    const float yj = ya - am1;
+                    rowof(Mv, r) = vi ? rowof(Mv, r) - xr : 0.0f;
+                    rowof(Mp, r) = vi ? rowof(Mp, r) - cs : 0.0f;
+                    rowof(Ma, r) = vi ? rowof(Ma, r) - ya : 0.0f;
+                    rowof(Mj, r) = (vi && i >= 1) ? rowof(Mj, r) - yj : 0.0f;
+                    xm1 = xr;
+                    am1 = ya;
+                }
+                rowof(Mv, HQ) = rowof(Mp, HQ) = rowof(Ma, HQ) = rowof(Mj, HQ) = 0.0f;
+            }
         }
         __syncthreads();   // the slab is read: A (which it occupies) is cleared for the MMA
         for (int e = tid; e < MROWS * KD; e += NTH) reinterpret_cast<float *>(As)[e] = 0.0f;
@@ -2868,16 +2926,21 @@ struct Variant {
     solve_fn admm, paper, admm_tc, paper_tc;       // one problem per launch
     solve_fn b_admm, b_paper, b_admm_tc, b_paper_tc;   // batched launches
     solve_fn admm_tc4, b_admm_tc4;                 // ADMM on the tensor cores, 4-warp blocks (M = 64)
+    // the ADMM tensor-core kernels that read warm-start inputs (x_init, dual_init);
+    // the ones above do not (fewer registers)
+    solve_fn admm_tc_w, b_admm_tc_w, admm_tc4_w, b_admm_tc4_w;
 };
 
 // The ADMM iteration with the tensor-core K-apply runs on solve_kernel_z; every
 // other combination on solve_kernel.
 #define VARIANT(HQv)                                                                                    \
     {HQv, solve_kernel<HQv, PRISM_MODE_ADMM, false, false>, solve_kernel<HQv, PRISM_MODE_PAPER, false, false>, \
-     solve_kernel_z<HQv, 8, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false>,                         \
+     solve_kernel_z<HQv, 8, false, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false>,                  \
      solve_kernel<HQv, PRISM_MODE_ADMM, false, true>, solve_kernel<HQv, PRISM_MODE_PAPER, false, true>,       \
-     solve_kernel_z<HQv, 8, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, true>,                           \
-     solve_kernel_z<HQv, 4, false>, solve_kernel_z<HQv, 4, true>}
+     solve_kernel_z<HQv, 8, true, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, true>,                    \
+     solve_kernel_z<HQv, 4, false, false>, solve_kernel_z<HQv, 4, true, false>,                               \
+     solve_kernel_z<HQv, 8, false, true>, solve_kernel_z<HQv, 8, true, true>,                                 \
+     solve_kernel_z<HQv, 4, false, true>, solve_kernel_z<HQv, 4, true, true>}
 // prev_variant_hq (used for the rows that always exist) must list the same chunks.
 constexpr int kVariantHQ[] = {3, 5, 7, 9, 11, 13, 15, 17, 21, 25, 29, 33};
 constexpr bool variant_chain_ok()
@@ -3018,7 +3081,7 @@ int z_warps(int hq)
 // one solve-kernel variant.  nw: warps of solve_kernel_z (ADMM on the tensor
 // cores; 0 = z_warps), ignored by the other kernels.
 prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, int MP_max, int device, int nw,
-                            solve_fn &fn, int &threads, size_t &smem, int &blocks_per_sm, int &hq)
+                            solve_fn &fn, int &threads, size_t &smem, int &blocks_per_sm, int &hq, bool warm)
 {
     const Variant *v = pick_variant(H);
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", H);
@@ -3035,10 +3098,14 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
                         : (batched ? solve_kernel_q8<13, true> : solve_kernel_q8<13, false>);
         smem = (size_t)solve_smem_q8(hq8).total;
     } else if (!batched) {
-        fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? v->admm_tc4 : v->admm_tc) : v->admm)
+        fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? (warm ? v->admm_tc4_w : v->admm_tc4)
+                                                        : (warm ? v->admm_tc_w : v->admm_tc))
+                                             : v->admm)
                                        : (tc ? v->paper_tc : v->paper);
     } else {
-        fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? v->b_admm_tc4 : v->b_admm_tc) : v->b_admm)
+        fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? (warm ? v->b_admm_tc4_w : v->b_admm_tc4)
+                                                        : (warm ? v->b_admm_tc_w : v->b_admm_tc))
+                                             : v->b_admm)
                                        : (tc ? v->b_paper_tc : v->b_paper);
     }
     threads = 32 * nw;
@@ -3067,7 +3134,7 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
 }
 
 prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t &smem, int &blocks_per_sm,
-                           int &grid, solve_fn &fn, int &threads)
+                           int &grid, solve_fn &fn, int &threads, bool warm = false)
 {
     v = pick_variant(h->H);
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", h->H);
@@ -3075,7 +3142,7 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
     int hq;
     const int nw = (tc && h->mode == PRISM_MODE_ADMM) ? handle_warps(h) : 0;
     prism_status st = variant_config(h->H, h->mode, tc, false, h->n, h->MP, h->device, nw, fn, threads, smem,
-                                     blocks_per_sm, hq);
+                                     blocks_per_sm, hq, warm);
     if (st) return st;
     const bool z = tc && h->mode == PRISM_MODE_ADMM;
     const int ntiles = solve_ntiles(batch, h->J, z ? (threads == 512 ? 64 : threads / 4) : 0);
@@ -3091,6 +3158,7 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
 struct PlanGroup {
     int hq = 0, mode = 0;
     bool tc = false;
+    bool warm = false;                 // some member starts from x_init / dual_init
     int nw = 8, threads = NTHREADS;    // warps and threads per block of the group's kernel
     std::vector<int> members;          // indices into the plan's problem list
     std::vector<SolveParams> params;   // with tile0 prefix sums
@@ -3442,7 +3510,7 @@ prism_status prism_proj_solve_ex(prism_proj_t h, int batch, const float *q0, con
     size_t smem;
     int bps, grid, threads;
     solve_fn fn;
-    st = launch_config(h, batch, v, smem, bps, grid, fn, threads);
+    st = launch_config(h, batch, v, smem, bps, grid, fn, threads, p.x_init != nullptr || p.dual_init != nullptr);
     if (st) return st;
     fn<<<grid, threads, smem, (cudaStream_t)cuda_stream>>>(single_launch(p));
     CUDA_TRY(cudaGetLastError());
@@ -3802,6 +3870,7 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
                 n_max = std::max(n_max, sp.n);
                 MP_max = std::max(MP_max, sp.MP);
                 Hmax = std::max(Hmax, sp.H);
+                if (sp.x_init || sp.dual_init) g.warm = true;
                 g.work += (double)sp.N * sp.J * (2.0 * (sp.H - 1) * (sp.H - 1) + 43.0 * sp.H);
                 g.params.push_back(sp);
             }
@@ -3812,7 +3881,8 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             g.lp.n_max = n_max;
             g.lp.MP_max = MP_max;
             int hq;
-            st = variant_config(Hmax, g.mode, g.tc, true, n_max, MP_max, dev, 0, g.fn, g.threads, g.smem, g.bps, hq);
+            st = variant_config(Hmax, g.mode, g.tc, true, n_max, MP_max, dev, 0, g.fn, g.threads, g.smem, g.bps, hq,
+                                g.warm);
             g.nw = g.threads / 32;
             g.hq = hq;
             if (!st && g.tc && g.mode == PRISM_MODE_ADMM) {
@@ -3896,7 +3966,7 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
                 alt.d_params = nullptr;
                 int hq;
                 st = variant_config(Hmax, alt.mode, alt.tc, true, alt.lp.n_max, alt.lp.MP_max, dev, cd.second, alt.fn,
-                                    alt.threads, alt.smem, alt.bps, hq);
+                                    alt.threads, alt.smem, alt.bps, hq, alt.warm);
                 if (st) break;
                 alt.nw = alt.threads / 32;
                 alt.hq = hq;
