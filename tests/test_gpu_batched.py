@@ -106,3 +106,39 @@ def test_autotune_reports_a_flag_raised_on_any_problem():
     for it in items:
         it["proj"].device_status()
         it["proj"].close()
+
+
+def test_plan_with_warm_starts_matches_single_solves():
+    """Problems that start from x_init / dual_init (a previous solve's iterate and
+    exported multiplier) run the plan group's warm-start kernel; each result
+    equals the single warm-started solve, and the cold members of the same plan
+    equal their single cold solves."""
+    import torch
+    iters = 40
+    items, batches = make_items(iters, seed=11)
+    warm_idx = [2, 3, 5]       # tensor-core and FP32-pipe problems
+    for k in warm_idx:
+        it = items[k]
+        x1, _, _, u1 = it["proj"].solve_ex(it["q0"], it["v0"], it["samples"], 25, want_dual_out=True)
+        it["x_init"], it["dual_init"] = x1.clone(), u1.clone()
+        # the warm start is applied to fresh samples of the same shape
+        it["samples"] = (it["samples"] + 0.3).contiguous()
+    torch.cuda.synchronize()
+    plan = pp.Plan(items, iters)
+    plan.launch()
+    torch.cuda.synchronize()
+    for k, (it, shape) in enumerate(zip(items, SHAPES)):
+        if shape[2] == 0:
+            continue
+        P = it["proj"]
+        if k in warm_idx:
+            x, pr, _, _ = P.solve_ex(it["q0"], it["v0"], it["samples"], iters, x_init=it["x_init"],
+                                     dual_init=it["dual_init"])
+        else:
+            x, pr, _ = P.solve(it["q0"], it["v0"], it["samples"], iters)
+        torch.cuda.synchronize()
+        assert float((it["out"] - x).abs().max()) <= 1e-5, k
+        assert float((it["primal"] - pr).abs().max()) <= 1e-6, k
+    plan.close()
+    for it in items:
+        it["proj"].close()
