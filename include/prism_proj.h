@@ -508,6 +508,8 @@ prism_status prism_test_set_device_flag(prism_proj_t h, int value);
  * passed as that call's dual_init and x_init.  W2 [K2][D + H] is fitted by
  * ridge regression on converged solves:
  *   (Phi^T Phi / n + lambda I) W2 = Phi^T Y / n   (FP64).
+ * The calls on one model are not to run concurrently (accumulate may grow its
+ * workspace); separate models are independent.
  * ------------------------------------------------------------------------ */
 typedef struct prism_ws_s *prism_ws_t;
 

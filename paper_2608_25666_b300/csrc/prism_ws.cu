@@ -705,9 +705,9 @@ prism_status prism_ws_create(prism_proj_t h, int hidden, const double *W1_host, 
     w->ZW = w->K2 + w->NO;
     w->device = device;
     w->d_bounds = bnd;
-    // the predictor's launch configuration: W2 resident in shared memory when two
-    // blocks still fit an SM, else streamed in chunks; blocks per SM from shared
-    // memory and from tensor memory (512 columns per SM)
+    // the predictor's launch configuration: blocks per SM from shared memory,
+    // registers and tensor memory (512 columns per SM), for each candidate width
+    // of the output-layer chunks
     int smem_sm = 0, smem_blk = 0, reserved = 0, sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -782,9 +782,9 @@ prism_status prism_ws_create(prism_proj_t h, int hidden, const double *W1_host, 
             e = cudaGetLastError();
         }
     }
-    // the predictor's launch configuration, once: its shared memory, and the
-    // resident blocks (shared memory, and 512 tensor-memory columns per SM)
-    if (e == cudaSuccess)
+    // the kernel's dynamic shared-memory limit is shared by every model in the
+    // process: only ever raise it
+    if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < w->smem)
         e = cudaFuncSetAttribute(ws_predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, w->smem);
     if (e == cudaSuccess) e = cudaMemset(w->d_G, 0, sizeof(double) * w->K2 * w->ZW);
     if (e == cudaSuccess) e = cudaMemset(w->d_W2p, 0, sizeof(uint16_t) * w->NOP * w->K2P);
