@@ -426,3 +426,32 @@ def test_shift_state_is_blockwise_shift(mode, steps):
     assert np.array_equal(xd.cpu().numpy(), xr)
     assert np.array_equal(ud.cpu().numpy(), ur)
     P.close()
+
+
+@pytest.mark.parametrize("mode,prec,tiling", [
+    (pp.MODE_ADMM, pp.PREC_TF32X3, 4), (pp.MODE_ADMM, pp.PREC_TF32X3, 8), (pp.MODE_ADMM, pp.PREC_TF32X3, 16),
+    (pp.MODE_ADMM, pp.PREC_FP32, 0), (pp.MODE_PAPER, pp.PREC_FP32, 0), (pp.MODE_PAPER, pp.PREC_TF32X3, 0),
+], ids=["tc4", "tc8", "q8", "simt", "paper-simt", "paper-tc"])
+def test_column_major_warm_start_on_every_kernel(mode, prec, tiling):
+    """Every solve kernel reads the column-major warm-start layout ([H][N*J],
+    [D][N*J]) as it reads the sample-major one: the same warm start in either
+    layout gives identical results (H = 64 so that the eight-quarter tiling
+    applies; N*J = 407 leaves ragged tiles)."""
+    import torch
+    J, H, N, dt = 11, 64, 37, 0.02
+    b = workloads.make_custom(71, N, J, H, dt, offset_sigma=0.5)
+    P = pp.Projector(J, H, dt, b["bounds"]).factor(1.0, mode, pp.SCALE_ROWNORM, prec)
+    if tiling:
+        P.set_tiling(tiling)
+    xi, q0, v0 = to_dev(b)
+    D = P.dual_rows()
+    x1, _, _, u1 = P.solve_ex(q0, v0, xi, 20, want_dual_out=True)
+    xi2 = (xi + 0.25).contiguous()
+    a = P.solve_ex(q0, v0, xi2, 30, x_init=x1, dual_init=u1, want_dual_out=True)
+    xc = x1.permute(1, 0, 2).reshape(H, N * J).contiguous()
+    uc = u1.permute(1, 0, 2).reshape(D, N * J).contiguous()
+    c = P.solve_ex(q0, v0, xi2, 30, x_init=xc, dual_init=uc, want_dual_out=True, init_layout=pp.INIT_COLUMN_MAJOR)
+    torch.cuda.synchronize()
+    for ta, tc in zip(a, c):
+        assert torch.equal(ta, tc)
+    P.close()
