@@ -668,7 +668,7 @@ def run_learned_ws(args):
     acc_cold = accuracy(cold)
     sweep = {}
     L_w = None
-    for L in [5, 10, 15, 20, 25, 30, 40, 50, 60, 80, 100]:
+    for L in [4, 6, 8, 10, 12, 15, 20, 25, 30, 40, 50, 60, 80, 100]:
         a = accuracy(warm_solve(L))
         sweep[L] = a
         if a["violation_max"] <= acc_cold["violation_max"] and a["dx_max"] <= acc_cold["dx_max"]:
