@@ -139,3 +139,36 @@ def test_warm_start_first_step_is_the_boundary_value():
     c = oracle.solve_batch(b["xi"], b["q0"], b["v0"], b["bounds"], dt, 7, 1.0, x_init=x0v, dual_init=u0,
                            want_dual_state=True)
     assert np.array_equal(a["x"], c["x"]) and np.array_equal(a["dual_state"], c["dual_state"])
+
+
+def test_first_layer_bias_and_relu_on_a_hand_computed_case():
+    """W1 = 0: every column's hidden layer is max(0, b1), whatever its features."""
+    F = np.array([[1.0, -2.0, 3.0], [0.5, 0.0, -1.0]])
+    Phi = ws.design(F, np.zeros((3, 3)), np.array([1.5, -0.5, 2.0]))
+    assert np.array_equal(Phi, np.array([[1.5, 0.0, 2.0, 1.0, -2.0, 3.0],
+                                         [1.5, 0.0, 2.0, 0.5, 0.0, -1.0]]))
+
+
+def test_predict_layout():
+    """A linear model (no hidden layer) whose output layer copies feature k into
+    output o (k = o mod H for the multiplier rows, k = step for the iterate)
+    returns dual_init[n][o][j] = xi[n][o mod H][j] / vmax_j and
+    x_init[n][k][j] = xi[n][k][j] / vmax_j."""
+    N, H, J = 3, 4, 2
+    D = 4 * H - 1
+    rng = np.random.default_rng(12)
+    xi = rng.normal(size=(N, H, J))
+    bounds = workloads.base_bounds(J)
+    bounds[3] = [2.0, 4.0]                                  # vmax per joint
+    W2 = np.zeros((H + 3, D + H))
+    for o in range(D):
+        W2[o % H, o] = 1.0
+    for k in range(H):
+        W2[k, D + k] = 1.0
+    x, u = ws.predict(xi, np.zeros(J), np.zeros(J), bounds, None, None, W2)
+    for n in range(N):
+        for j in range(J):
+            for o in range(D):
+                assert u[n, o, j] == xi[n, o % H, j] / bounds[3][j]
+            for k in range(H):
+                assert x[n, k, j] == xi[n, k, j] / bounds[3][j]
