@@ -943,8 +943,8 @@ def main():
     plain_ms = [pe[s].elapsed_time(pe[s + 1]) for s in range(args.plain_steps)]
     plain_value = w.N * args.plain_steps / (pe[0].elapsed_time(pe[-1]) / 1e3)
 
-    # ---- end to end through the host-buffer C-ABI call (pinned host memory, which
-    # the solve reads and writes in place through its device mapping)
+    # ---- end to end through the host-buffer C-ABI call on pinned host memory (the
+    # call pipelines chunk copies and solves on the handle's streams)
     hx = [torch.from_numpy(workloads.make_batch(w, step=rank * N_INPUTS + s)["xi"]).pin_memory()
           for s in range(4)]
     hq0 = torch.from_numpy(workloads.make_batch(w, step=0)["q0"]).pin_memory()
@@ -954,6 +954,10 @@ def main():
     hdu = torch.empty((w.N, w.J), dtype=torch.float32).pin_memory()
     for s in range(3):
         P.solve_host(hq0, hv0, hx[s % 4], w.iters, out=hout, primal=hpr, dual=hdu)
+    # the library's automatic chunk count for this batch (samples of 0.75 MB a chunk
+    # from 4 MB up; at most 16)
+    nbytes = 4 * w.N * w.H * w.J
+    q_chunks = 1 if nbytes < 4 * (1 << 20) else max(1, min(16, w.N, int(nbytes / 0.75e6 + 0.5)))
     barrier(ws)
     t0 = time.perf_counter()
     for s in range(args.e2e_steps):
@@ -1042,9 +1046,11 @@ def main():
                 "fp32_pipe": fp32_pipe,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-                        "api": "prism_proj_solve_host on pinned host buffers, one call per step (the solve "
-                               "reads xi from and writes x and the residuals into the mapped host buffers: "
-                               "the bytes cross the bus inside the kernel, overlapping other tiles' iterations)"},
+                        "api": "prism_proj_solve_host on pinned host buffers, one call per step (the call "
+                               "cuts the batch into chunks that are copied in, solved and copied out on the "
+                               "handle's streams, one chunk's copies overlapping other chunks' solves; the "
+                               "residuals are written into the mapped host buffers)",
+                        "host_chunks": q_chunks},
                 "e2e_pipelined": {"value": e2e_pipe_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                                   "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                                   "api": "prism_proj_solve on two streams, pinned-host copies around "

@@ -219,12 +219,17 @@ prism_status prism_proj_solve_plain(prism_proj_t h, int batch, const float *q0, 
  * arrays, layouts as above).  q0 and v0 are copied to a device staging buffer
  * owned by the handle.  When samples and out are both page-locked and mapped
  * into this device's address space (cudaHostAlloc, pinned torch tensors,
- * cudaHostRegister with cudaHostRegisterMapped), the solve reads xi from and
- * writes x into them directly, so the transfers overlap the iteration of the
- * other tiles; samples == out is allowed.  Otherwise samples are copied to the
- * staging buffer, solved in place there and x is copied back.  Each residual
+ * cudaHostRegister with cudaHostRegisterMapped), the batch is cut into chunks
+ * of whole samples that flow through a pipeline: each chunk is copied in, solved
+ * in place in the staging buffer and copied out, on streams of the handle
+ * ordered by events, so that one chunk's copies overlap other chunks' solves
+ * (prism_proj_set_host_chunks sets the number of chunks); with one chunk the
+ * solve reads xi from and writes x into the mapped buffers directly.
+ * samples == out is allowed.  Otherwise (pageable memory) samples are copied to
+ * the staging buffer, solved in place there and x is copied back.  Each residual
  * array (when not NULL) is written directly if mapped, else copied back.
- * Synchronises cuda_stream before returning; a device-side wait that ran out
+ * The work is ordered after what cuda_stream holds at the call; the call
+ * synchronises cuda_stream before returning; a device-side wait that ran out
  * during the solve returns PRISM_ERR_TIMEOUT.  Host buffers must not be
  * freed or unpinned before the call returns.
  */
@@ -281,6 +286,18 @@ prism_status prism_proj_query(prism_proj_t h, int batch, long long out[8]);
  * same iteration up to FP32 rounding order.  Plans choose their own tiling.
  */
 prism_status prism_proj_set_tiling(prism_proj_t h, int warps);
+
+/*
+ * prism_proj_set_host_chunks -- how prism_proj_solve_host moves page-locked,
+ * mapped host buffers (the paper has no counterpart: a transfer schedule).
+ *   chunks: 0 the library's choice (chunks of about 0.75 MB of samples, one
+ *   chunk below 4 MB); 1 one solve that reads and writes the host buffers
+ *   directly; 2..PRISM_HOST_MAX_CHUNKS that many chunks (fewer when the batch
+ *   has fewer samples).  Results do not depend on it: every column is solved by
+ *   the same kernel with the same arithmetic.  Else PRISM_ERR_INVALID_ARG.
+ */
+#define PRISM_HOST_MAX_CHUNKS 16
+prism_status prism_proj_set_host_chunks(prism_proj_t h, int chunks);
 
 /*
  * prism_proj_solve_plain_noalloc -- prism_proj_solve_plain for callers that

@@ -34,6 +34,7 @@ _lib = None
 
 
 INIT_SAMPLE_MAJOR, INIT_COLUMN_MAJOR = 0, 1   # warm-start input layouts of prism_proj_solve_ex
+HOST_MAX_CHUNKS = 16          # PRISM_HOST_MAX_CHUNKS: most chunks of the host-buffer pipeline
 
 
 class SolveOpts(ctypes.Structure):
@@ -93,6 +94,8 @@ def lib() -> ctypes.CDLL:
             L.prism_test_set_device_flag.restype = i
             L.prism_proj_set_tiling.argtypes = [P, i]
             L.prism_proj_set_tiling.restype = i
+            L.prism_proj_set_host_chunks.argtypes = [P, i]
+            L.prism_proj_set_host_chunks.restype = i
             for name in ("create", "factor", "solve", "solve_ex", "solve_plain", "solve_host",
                          "check_fp64", "shift_state", "get_factor", "query", "device_status", "destroy"):
                 getattr(L, "prism_proj_" + name).restype = i
@@ -346,6 +349,11 @@ class Projector:
     def set_tiling(self, warps: int):
         """prism_proj_set_tiling: 0 default, 4 / 8 (four quarters), 16 (eight quarters)."""
         _check(lib().prism_proj_set_tiling(self._h, int(warps)))
+        return self
+
+    def set_host_chunks(self, chunks: int):
+        """prism_proj_set_host_chunks: 0 automatic, 1 one solve on the mapped buffers, else chunks."""
+        _check(lib().prism_proj_set_host_chunks(self._h, int(chunks)))
         return self
 
     def query(self, batch: int) -> dict:

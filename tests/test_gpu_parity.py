@@ -202,6 +202,76 @@ def test_host_entry_point_on_pinned_buffers(prec, J, H, N, dt, how):
     P.close()
 
 
+@pytest.mark.parametrize("prec", [pp.PREC_TF32X3, pp.PREC_FP32], ids=["tc", "simt"])
+@pytest.mark.parametrize("J,H,N,dt,chunks", [
+    (12, 50, 203, 0.02, 3),      # ragged last chunk, chunks of whole 32-column tiles
+    (7, 33, 37, 0.05, 16),       # chunks of 3 samples; the last one shorter
+    (1, 20, 5, 0.05, 16),        # more chunks asked for than samples
+    (12, 50, 96, 0.02, 2),
+])
+@pytest.mark.parametrize("how", ["pinned", "in_place", "pageable_residuals"])
+def test_host_pipeline_chunks(prec, J, H, N, dt, chunks, how):
+    """The host pipeline (chunks copied in, solved in place in the staging
+    buffer and copied out, on the handle's streams) equals the solve on device
+    buffers bit for bit for any chunk count, in place (samples is out), and
+    with residuals in pageable memory (copied back per chunk)."""
+    import torch
+    b = workloads.make_custom(90 + J, N, J, H, dt)
+    P = pp.Projector(J, H, dt, b["bounds"]).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, prec)
+    xi, q0, v0 = to_dev(b)
+    xd, pd, dd = P.solve(q0, v0, xi, 40)
+    torch.cuda.synchronize()
+    P.set_host_chunks(chunks)
+    hx = torch.from_numpy(b["xi"]).pin_memory()
+    if how == "pageable_residuals":
+        hpr = np.full((N, J), np.nan, dtype=np.float32)
+        hdu = np.full((N, J), np.nan, dtype=np.float32)
+    else:
+        hpr = torch.full((N, J), float("nan")).pin_memory()
+        hdu = torch.full((N, J), float("nan")).pin_memory()
+    hout = hx if how == "in_place" else torch.full((N, H, J), float("nan")).pin_memory()
+    for _ in range(2):               # a second call reuses the streams, events and staging
+        if how == "in_place":
+            hx.copy_(torch.from_numpy(b["xi"]))
+        xo, pr, du = P.solve_host(b["q0"], b["v0"], hx, 40, out=hout, primal=hpr, dual=hdu)
+        pr = pr.numpy() if isinstance(pr, torch.Tensor) else pr
+        du = du.numpy() if isinstance(du, torch.Tensor) else du
+        assert np.array_equal(xo.numpy(), xd.cpu().numpy())
+        assert np.array_equal(pr, pd.cpu().numpy()) and np.array_equal(du, dd.cpu().numpy())
+        if how != "in_place":
+            assert np.array_equal(hx.numpy(), b["xi"])
+    with pytest.raises(pp.PrismError) as e:
+        P.set_host_chunks(pp.HOST_MAX_CHUNKS + 1)
+    assert e.value.status == 1
+    g = {"x": xd.cpu().numpy().astype(np.float64), "primal": pd.cpu().numpy().astype(np.float64),
+         "dual": dd.cpu().numpy().astype(np.float64)}
+    cols = np.unique(np.linspace(0, N * J - 1, min(N * J, 16)).astype(np.int64))
+    assert_parity(g, oracle_solve(b, 40, 1.0, cols=cols), cols=cols, dual_tol=2e-4)
+    P.close()
+
+
+def test_host_pipeline_automatic_at_full_size():
+    """At the realistic size (9.8 MB of samples) the automatic choice pipelines
+    the pinned buffers; the result equals the device solve bit for bit, and an
+    argument error (rho mismatch) is reported before anything is enqueued."""
+    import torch
+    b = workloads.make_custom(97, 4096, 12, 50, 0.02)
+    P = pp.Projector(12, 50, 0.02, b["bounds"]).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, pp.PREC_TF32X3)
+    xi, q0, v0 = to_dev(b)
+    xd, pd, dd = P.solve(q0, v0, xi, 30)
+    torch.cuda.synchronize()
+    hx = torch.from_numpy(b["xi"]).pin_memory()
+    hout = torch.full_like(hx, float("nan")).pin_memory()
+    hpr = torch.full((4096, 12), float("nan")).pin_memory()
+    hdu = torch.full((4096, 12), float("nan")).pin_memory()
+    P.solve_host(b["q0"], b["v0"], hx, 30, out=hout, primal=hpr, dual=hdu)
+    assert torch.equal(hout, xd.cpu()) and torch.equal(hpr, pd.cpu()) and torch.equal(hdu, dd.cpu())
+    with pytest.raises(pp.PrismError) as e:
+        P.solve_host(b["q0"], b["v0"], hx, 30, rho=2.0, out=hout)
+    assert e.value.status == 3
+    P.close()
+
+
 def test_fp64_check_matches_oracle_residual():
     import torch
     b = workloads.make_custom(8, 30, 12, 30, 0.05)
