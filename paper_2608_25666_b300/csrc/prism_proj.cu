@@ -845,6 +845,21 @@ __global__ void diag_wait_kernel(uint32_t limit, int *flag)
 __host__ __device__ constexpr int tc_hq4(int hq) { return round_up(hq, 4); }
 __host__ __device__ constexpr int tc_kd(int hq) { return 4 * tc_hq4(hq); }
 __host__ __device__ constexpr int tc_nrows(int hq) { return round_up(4 * hq, 8); }
+// solve_kernel_z packs the reduction without padding: quarter b owns the S =
+// HQ + 1 consecutive K indices [S b, S b + S) (its HQ right-hand-side rows, then
+// its spare slot), so every K-step of 8 still sums consecutive time steps (plus
+// at most one spare slot) and K = 4 S is a multiple of 8 (HQ is odd).  Inside
+// each aligned group of 4 indices the word is XOR-ed with the owner's key x(b)
+// (b when S % 4 == 0, else b / 2: the two quarters sharing a group at a quarter
+// boundary then have the same key), so the four quarter-threads of a column,
+// storing the same row r together, hit four different words (banks).
+__host__ __device__ constexpr int z_kd(int hq) { return 4 * (hq + 1); }
+__host__ __device__ constexpr int z_key(int hq, int b) { return ((hq + 1) & 3) ? (b >> 1) : b; }
+// K index of row r (r <= HQ; r == HQ the spare slot) of quarter b
+__host__ __device__ constexpr int z_slot(int hq, int b, int r)
+{
+    return (((hq + 1) * b + r) & ~3) | ((((hq + 1) * b + r) & 3) ^ z_key(hq, b));
+}
 // Tensor-memory columns per block: D holds the products with the high parts of
 // B in columns [0, ND) and with the low parts in [ND, 2 ND).
 __host__ __device__ constexpr int tc_tmem_cols(int hq)
@@ -1579,7 +1594,7 @@ __host__ __device__ constexpr int z_xi_stride(int hq) { return 2 * (((hq + 1) / 
 // eight warps, M = 64 for four.
 __host__ __device__ inline ZSmem solve_smem_z(int hq, int nw)
 {
-    const int KD = tc_kd(hq), ND = tc_nrows(hq), NP = (hq + 1) / 2;
+    const int KD = z_kd(hq), ND = tc_nrows(hq), NP = (hq + 1) / 2;
     ZSmem L;
     int off = 0;
     L.a = off;   off += 16 * nw * KD * 4;                // A operand; the tile slab outside the iteration
@@ -1634,7 +1649,7 @@ __global__ void stage_z_kernel(int HQ, int n, int H, const float *__restrict__ K
                                const float *__restrict__ wp, float wa0, float wa, float wj0, float wj,
                                float *__restrict__ Bz, float *__restrict__ Wz)
 {
-    const int KD = tc_kd(HQ), ND = tc_nrows(HQ), HQ4 = tc_hq4(HQ), NP = (HQ + 1) / 2;
+    const int KD = z_kd(HQ), ND = tc_nrows(HQ), S = HQ + 1, NP = (HQ + 1) / 2;
     const int KW = n + 4;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
     for (int e = t0; e < 2 * ND * KD; e += nt) {
@@ -1644,12 +1659,14 @@ __global__ void stage_z_kernel(int HQ, int n, int H, const float *__restrict__ K
         const int xt = (pc & 3) * HQ + (pc >> 2);   // time step of D column pc
         const bool prefix = pc >= 4 * HQ;           // column 4HQ + b: quarter b's prefix sum
         const int i = prefix ? n + (pc & 3) : xt - 1;
-        const int kb_ = kq / HQ4, kr = kq - kb_ * HQ4;
-        const int rr = (kr & ~3) | ((kr & 3) ^ kb_);  // local row stored in this slot
+        // the quarter and row stored in this slot (z_slot inverted: the key is
+        // that of the first quarter in the slot's group of 4)
+        const int k0 = (kq & ~3) | ((kq & 3) ^ z_key(HQ, (kq & ~3) / S));
+        const int kb_ = k0 / S, rr = k0 - kb_ * S;
         const int xk = kb_ * HQ + rr;
         int j = -1;
         if (rr < HQ) j = (xk >= 1 && xk <= n) ? xk - 1 : -1;
-        else if (rr == HQ) j = (kb_ == 0) ? n : n + kb_;
+        else j = (kb_ == 0) ? n : n + kb_;
         const bool in = (prefix || (xt >= 1 && xt <= n)) && j >= 0;
         const int src = i * KW + j;
         Bz[cm_off(pr, kq, KD) >> 2] = in ? (low ? Klo[src] : Khi[src]) : 0.0f;
@@ -1702,12 +1719,12 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
     constexpr int HP = 4 * HQ;
     constexpr int CP = z_col_stride(NW);
     constexpr int TMEM_COLS = tc_tmem_cols(HQ);
-    constexpr int KD = tc_kd(HQ), ND = tc_nrows(HQ), HQ4 = tc_hq4(HQ);
+    constexpr int KD = z_kd(HQ), ND = tc_nrows(HQ);
     constexpr int NP = (HQ + 1) / 2;   // row pairs; the second row of the last pair is a spare
     static_assert(HQ & 1, "row pairs assume an odd horizon chunk (one spare row)");
     static_assert(tc_nrows(HQ) + 16 * ((HQ + 1 + 3) / 4) <= tc_tmem_cols(HQ),
                   "the readback reads past the tensor-memory allocation");
-    static_assert((4 * HQ + 2) * z_col_stride(NW) <= 16 * NW * tc_kd(HQ), "the tile slab must fit in the A operand");
+    static_assert((4 * HQ + 2) * z_col_stride(NW) <= 16 * NW * z_kd(HQ), "the tile slab must fit in the A operand");
     static_assert(NW == 4 || NW == 8, "M = 64 or 128");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t tmem_slot;
@@ -1733,12 +1750,16 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
     // one 16x128b load hands thread t lanes t/4 and t/4 + 8: both rows of its column.
     const int arow_hi = (NW == 8) ? 32 * (warp & 3) + 16 * (warp >> 2) + (lane >> 2) : 16 * warp + (lane >> 2);
     const int tl_lane = (NW == 8) ? 32 * (warp & 3) + 16 * (warp >> 2) : 32 * warp;
-    // local row r goes to word (r & 3) ^ b of 16-byte slot r >> 2 of this quarter's K block
-    float *ahi = reinterpret_cast<float *>(As + cm_off(arow_hi, HQ4 * b, KD));
+    // local row r goes to K index z_slot(HQ, b, r); z_slot(r + 4t) = z_slot(r) + 4t,
+    // so row r is stored at aw[r & 3] + 32 (r >> 2) (a group of 4 indices is 32 floats)
+    float *arow = reinterpret_cast<float *>(As + cm_off(arow_hi, 0, KD));
     constexpr int LO = 8 * KD;   // floats from a column's high row to its low row
     float *aw[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) aw[m] = ahi + (m ^ b);
+    for (int m = 0; m < 4; ++m) {
+        const int k = z_slot(HQ, b, m);
+        aw[m] = arow + 32 * (k >> 2) + (k & 3);
+    }
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -3439,7 +3460,7 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
         float *Khi8 = nullptr, *Klo8 = nullptr, *Bz = nullptr, *Wz = nullptr;
         const Variant *zv = pick_variant(H);
         if (e == cudaSuccess && zv && tc_fits(H)) {
-            e = dev_malloc(&Bz, sizeof(float) * 2 * tc_nrows(zv->hq) * tc_kd(zv->hq));
+            e = dev_malloc(&Bz, sizeof(float) * 2 * tc_nrows(zv->hq) * z_kd(zv->hq));
             if (e == cudaSuccess) e = dev_malloc(&Wz, sizeof(float) * 3 * 8 * ((zv->hq + 1) / 2));
         }
         if (e == cudaSuccess && q8_capable(H)) {
