@@ -860,6 +860,21 @@ __host__ __device__ constexpr int z_slot(int hq, int b, int r)
 {
     return (((hq + 1) * b + r) & ~3) | ((((hq + 1) * b + r) & 3) ^ z_key(hq, b));
 }
+// The kernel's store addresses (two bases and a word XOR per quarter-thread, in
+// floats from the row start: a group of 4 K indices is 32 floats) agree with
+// z_slot for every quarter and row: checked at compile time.
+__host__ __device__ constexpr bool z_store_form_ok(int hq)
+{
+    for (int b = 0; b < 4; ++b) {
+        const int sb = (hq + 1) * b, off = sb & 3, key2 = off ^ z_key(hq, b);
+        for (int r = 0; r <= hq; ++r) {
+            const int m = r & 3, k = z_slot(hq, b, r);
+            const int addr = 8 * (sb - off) + ((m & 2) ? 16 * off : 0) + (m ^ key2) + 32 * (r >> 2);
+            if (addr != 32 * (k >> 2) + (k & 3)) return false;
+        }
+    }
+    return true;
+}
 // Tensor-memory columns per block: D holds the products with the high parts of
 // B in columns [0, ND) and with the low parts in [ND, 2 ND).
 __host__ __device__ constexpr int tc_tmem_cols(int hq)
@@ -1594,13 +1609,13 @@ __host__ __device__ constexpr int z_xi_stride(int hq) { return 2 * (((hq + 1) / 
 // eight warps, M = 64 for four.
 __host__ __device__ inline ZSmem solve_smem_z(int hq, int nw)
 {
-    const int KD = z_kd(hq), ND = tc_nrows(hq), NP = (hq + 1) / 2;
+    const int KD = z_kd(hq), ND = tc_nrows(hq);
     ZSmem L;
     int off = 0;
     L.a = off;   off += 16 * nw * KD * 4;                // A operand; the tile slab outside the iteration
     L.bhi = off; off += 2 * ND * KD * 4;                 // B: high parts over low parts (N-stacked)
     L.xi = off;  off += 32 * nw * z_xi_stride(hq) * 4;   // xi, each quarter-thread's rows contiguous
-    L.wt = off;  off += 3 * 4 * NP * 8;                  // weight pairs: position, acceleration, jerk x quarter x pair
+    L.wt = off;  off += 3 * 4 * ((hq + 1) / 2) * 8;      // weight pairs: position, acceleration, jerk x quarter x pair
     L.cb = off;  off += PRISM_MAX_J * (int)sizeof(ColBounds);   // each joint's bounds, computed once per problem
     L.total = off;
     return L;
@@ -1725,6 +1740,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
     static_assert(tc_nrows(HQ) + 16 * ((HQ + 1 + 3) / 4) <= tc_tmem_cols(HQ),
                   "the readback reads past the tensor-memory allocation");
     static_assert((4 * HQ + 2) * z_col_stride(NW) <= 16 * NW * z_kd(HQ), "the tile slab must fit in the A operand");
+    static_assert(z_store_form_ok(HQ), "staging addresses disagree with the K layout");
     static_assert(NW == 4 || NW == 8, "M = 64 or 128");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t tmem_slot;
@@ -1750,15 +1766,18 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
     // one 16x128b load hands thread t lanes t/4 and t/4 + 8: both rows of its column.
     const int arow_hi = (NW == 8) ? 32 * (warp & 3) + 16 * (warp >> 2) + (lane >> 2) : 16 * warp + (lane >> 2);
     const int tl_lane = (NW == 8) ? 32 * (warp & 3) + 16 * (warp >> 2) : 32 * warp;
-    // local row r goes to K index z_slot(HQ, b, r); z_slot(r + 4t) = z_slot(r) + 4t,
-    // so row r is stored at aw[r & 3] + 32 (r >> 2) (a group of 4 indices is 32 floats)
-    float *arow = reinterpret_cast<float *>(As + cm_off(arow_hi, 0, KD));
+    // local row r goes to K index z_slot(HQ, b, r), stored at aw[r & 3] + 32 (r >> 2)
+    // (a group of 4 indices is 32 floats).  With sb = (HQ + 1) b and off = sb % 4 (0 or
+    // 2): z_slot = sb - off + 4 [r % 4 + off >= 4] + 4 (r / 4) + ((r % 4) ^ off ^ key),
+    // so the four pointers are two bases and a word XOR (cheap to keep or rebuild)
     constexpr int LO = 8 * KD;   // floats from a column's high row to its low row
     float *aw[4];
+    {
+        const int sb = (HQ + 1) * b, off = sb & 3, key2 = off ^ z_key(HQ, b);
+        float *p0 = reinterpret_cast<float *>(As + cm_off(arow_hi, 0, KD)) + 8 * (sb - off);
+        float *p1 = p0 + 16 * off;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const int k = z_slot(HQ, b, m);
-        aw[m] = arow + 32 * (k >> 2) + (k & 3);
+        for (int m = 0; m < 4; ++m) aw[m] = ((m & 2) ? p1 : p0) + (m ^ key2);
     }
 
     if (warp == 0) {
