@@ -854,6 +854,19 @@ __host__ __device__ constexpr int tc_nrows(int hq) { return round_up(4 * hq, 8);
 // boundary then have the same key), so the four quarter-threads of a column,
 // storing the same row r together, hit four different words (banks).
 __host__ __device__ constexpr int z_kd(int hq) { return 4 * (hq + 1); }
+// solve_kernel_z's operand B holds its tf32 high parts and its remainders as two
+// parts of NDP = ND rounded up to 16 rows (an M = 128 MMA takes N in steps of
+// 16; rows past ND are zero).  Both parts are applied by MMAs into the SAME
+// accumulator (the high parts, then the remainders), so D has ND columns and a
+// column's x is the sum of its two A rows' entries.
+__host__ __device__ constexpr int z_ndp(int hq) { return round_up(tc_nrows(hq), 16); }
+// Tensor-memory columns of solve_kernel_z: D's ND columns and the 16-column
+// groups the readback loads, rounded up to a power of two (at least 32).
+__host__ __device__ constexpr int z_tmem_cols(int hq)
+{
+    const int need = tc_nrows(hq) > 16 * ((hq + 1 + 3) / 4) ? tc_nrows(hq) : 16 * ((hq + 1 + 3) / 4);
+    return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+}
 __host__ __device__ constexpr int z_key(int hq, int b) { return ((hq + 1) & 3) ? (b >> 1) : b; }
 // K index of row r (r <= HQ; r == HQ the spare slot) of quarter b
 __host__ __device__ constexpr int z_slot(int hq, int b, int r)
@@ -1595,6 +1608,44 @@ __device__ __forceinline__ void tmem_read_x(uint32_t taddr, bool split, float ou
     }
 }
 
+// solve_kernel_z's readback: this quarter-thread's x (KN - 1 time steps) and its
+// prefix sum (index KN - 1) from the accumulator, where time step k sits in D
+// column 4k + t%4, lanes t/4 (the products of the right-hand side's high parts)
+// and t/4 + 8 (of its remainders); a 16x128b.x4 load at column 16g hands thread
+// t, in registers 2m and 2m + 1, both lanes of column 16g + 4m + t%4, and x is
+// their sum (B's high parts and remainders already share the accumulator).
+template <int KN>
+__device__ __forceinline__ void tmem_read_x1(uint32_t taddr, float out[KN])
+{
+    constexpr int NL = (KN + 3) / 4;
+#pragma unroll
+    for (int g0 = 0; g0 < NL; g0 += 2) {
+        uint32_t h[2][8];
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            if (g0 + g < NL) {
+                asm volatile("tcgen05.ld.sync.aligned.16x128b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                             : "=r"(h[g][0]), "=r"(h[g][1]), "=r"(h[g][2]), "=r"(h[g][3]), "=r"(h[g][4]),
+                               "=r"(h[g][5]), "=r"(h[g][6]), "=r"(h[g][7])
+                             : "r"(taddr + (uint32_t)(16 * (g0 + g))));
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) h[g][e] = 0u;
+            }
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(h[0][0]), "+r"(h[0][1]), "+r"(h[0][2]), "+r"(h[0][3]), "+r"(h[0][4]), "+r"(h[0][5]), "+r"(h[0][6]), "+r"(h[0][7]), "+r"(h[1][0]), "+r"(h[1][1]), "+r"(h[1][2]), "+r"(h[1][3]), "+r"(h[1][4]), "+r"(h[1][5]), "+r"(h[1][6]), "+r"(h[1][7])
+                     :: "memory");
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int k = 4 * (g0 + g) + m;
+                if (k < KN) out[k] = __uint_as_float(h[g][2 * m]) + __uint_as_float(h[g][2 * m + 1]);
+            }
+    }
+}
+
 // Shared-memory carve-up of solve_kernel_z (byte offsets).
 struct ZSmem {
     int a, bhi, xi, wt, cb, total;
@@ -1613,7 +1664,7 @@ __host__ __device__ inline ZSmem solve_smem_z(int hq, int nw)
     ZSmem L;
     int off = 0;
     L.a = off;   off += 16 * nw * KD * 4;                // A operand; the tile slab outside the iteration
-    L.bhi = off; off += 2 * ND * KD * 4;                 // B: high parts over low parts (N-stacked)
+    L.bhi = off; off += 2 * z_ndp(hq) * KD * 4;          // B: high parts, then low parts (NDP rows each)
     L.xi = off;  off += 32 * nw * z_xi_stride(hq) * 4;   // xi, each quarter-thread's rows contiguous
     L.wt = off;  off += 3 * 4 * ((hq + 1) / 2) * 8;      // weight pairs: position, acceleration, jerk x quarter x pair
     L.cb = off;  off += PRISM_MAX_J * (int)sizeof(ColBounds);   // each joint's bounds, computed once per problem
@@ -1664,13 +1715,13 @@ __global__ void stage_z_kernel(int HQ, int n, int H, const float *__restrict__ K
                                const float *__restrict__ wp, float wa0, float wa, float wj0, float wj,
                                float *__restrict__ Bz, float *__restrict__ Wz)
 {
-    const int KD = z_kd(HQ), ND = tc_nrows(HQ), S = HQ + 1, NP = (HQ + 1) / 2;
+    const int KD = z_kd(HQ), ND = tc_nrows(HQ), NDP = z_ndp(HQ), S = HQ + 1, NP = (HQ + 1) / 2;
     const int KW = n + 4;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    for (int e = t0; e < 2 * ND * KD; e += nt) {
+    for (int e = t0; e < 2 * NDP * KD; e += nt) {
         const int pr = e / KD, kq = e - pr * KD;
-        const bool low = pr >= ND;
-        const int pc = low ? pr - ND : pr;
+        const bool low = pr >= NDP;
+        const int pc = low ? pr - NDP : pr;   // D column (rows pc >= ND are zero)
         const int xt = (pc & 3) * HQ + (pc >> 2);   // time step of D column pc
         const bool prefix = pc >= 4 * HQ;           // column 4HQ + b: quarter b's prefix sum
         const int i = prefix ? n + (pc & 3) : xt - 1;
@@ -1682,7 +1733,7 @@ __global__ void stage_z_kernel(int HQ, int n, int H, const float *__restrict__ K
         int j = -1;
         if (rr < HQ) j = (xk >= 1 && xk <= n) ? xk - 1 : -1;
         else j = (kb_ == 0) ? n : n + kb_;
-        const bool in = (prefix || (xt >= 1 && xt <= n)) && j >= 0;
+        const bool in = pc < ND && (prefix || (xt >= 1 && xt <= n)) && j >= 0;
         const int src = i * KW + j;
         Bz[cm_off(pr, kq, KD) >> 2] = in ? (low ? Klo[src] : Khi[src]) : 0.0f;
     }
@@ -1733,12 +1784,12 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
     constexpr int MROWS = 16 * NW;      // rows of A (the MMA's M)
     constexpr int HP = 4 * HQ;
     constexpr int CP = z_col_stride(NW);
-    constexpr int TMEM_COLS = tc_tmem_cols(HQ);
+    constexpr int TMEM_COLS = z_tmem_cols(HQ);
     constexpr int KD = z_kd(HQ), ND = tc_nrows(HQ);
     constexpr int NP = (HQ + 1) / 2;   // row pairs; the second row of the last pair is a spare
     static_assert(HQ & 1, "row pairs assume an odd horizon chunk (one spare row)");
-    static_assert(tc_nrows(HQ) + 16 * ((HQ + 1 + 3) / 4) <= tc_tmem_cols(HQ),
-                  "the readback reads past the tensor-memory allocation");
+    static_assert(16 * ((HQ + 1 + 3) / 4) <= z_tmem_cols(HQ) && tc_nrows(HQ) <= z_tmem_cols(HQ),
+                  "the accumulator or the readback exceeds the tensor-memory allocation");
     static_assert((4 * HQ + 2) * z_col_stride(NW) <= 16 * NW * z_kd(HQ), "the tile slab must fit in the A operand");
     static_assert(z_store_form_ok(HQ), "staging addresses disagree with the K layout");
     static_assert(NW == 4 || NW == 8, "M = 64 or 128");
@@ -1824,7 +1875,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
             // per-problem operand B = [K' | kb' | C] (tf32 high parts over low parts,
             // with the quarter-prefix rows) and the weight pairs, staged at factor
             // time in this layout (stage_z_kernel): plain 16-byte copies
-            copy16_smem<ZCOPY>(smem_raw + L.bhi, p.Bz, 2 * ND * KD * 4, tid, NTH);
+            copy16_smem<ZCOPY>(smem_raw + L.bhi, p.Bz, 2 * z_ndp(HQ) * KD * 4, tid, NTH);
             copy16_smem<ZCOPY>(smem_raw + L.wt, p.Wz, 3 * 8 * NP * 4, tid, NTH);
             // the bounds of each joint (FP64 arithmetic, rounded once): one thread per
             // joint here instead of every thread on every tile
@@ -2138,17 +2189,28 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
                 aborted = true;
                 break;
             }
-            // ---- a5: K-apply, one M = 128 MMA per K-step (as in solve_kernel)
+            // ---- a5: K-apply: (split) the MMAs of B's remainders, then those of its high
+            // parts, all into one accumulator (N = ND for M = 64, NDP for M = 128): the
+            // small products are summed among themselves before the large ones arrive
             if (warp == 0) {
-                const uint32_t idesc = umma_idesc_tf32(MROWS, split ? 2 * ND : round_up(ND, NW == 8 ? 16 : 8));
+                constexpr int NDP = z_ndp(HQ);
+                const uint32_t idesc = umma_idesc_tf32(MROWS, NW == 8 ? NDP : ND);
                 const uint32_t sbo = (uint32_t)(KD >> 2) * 128u;
                 const uint64_t da = umma_desc(smem_addr(As), 128u, sbo);
                 const uint64_t db = umma_desc(smem_addr(smem_raw + L.bhi), 128u, sbo);
+                const uint64_t dl = umma_desc(smem_addr(smem_raw + L.bhi + (NDP >> 3) * sbo), 128u, sbo);
                 if (elect_one()) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t d1 = split ? dl : db;   // the first pass: remainders when split
                     for (int ks = 0; ks < (KD >> 3); ++ks) {
                         const uint64_t kk = (uint64_t)(16 * ks);
-                        umma_tf32(tbase, da + kk, db + kk, idesc, ks > 0 ? 1u : 0u);
+                        umma_tf32(tbase, da + kk, d1 + kk, idesc, ks > 0 ? 1u : 0u);
+                    }
+                    if (split) {
+                        for (int ks = 0; ks < (KD >> 3); ++ks) {
+                            const uint64_t kk = (uint64_t)(16 * ks);
+                            umma_tf32(tbase, da + kk, db + kk, idesc, 1u);
+                        }
                     }
                     umma_commit(smem_addr(&mma_bar));
                 }
@@ -2162,7 +2224,7 @@ solve_kernel_z(const __grid_constant__ LaunchParams P)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t tl = tbase + ((uint32_t)tl_lane << 16);
                 float xn[2 * NP];   // rows, then the sum of x over the earlier quarters
-                tmem_read_x<HQ + 1, ND>(tl, split, xn);
+                tmem_read_x1<HQ + 1>(tl, xn);
                 if (b == 0) xn[0] = colv ? v0j : 0.0f;   // x_0 = v0 exactly
                 if (last) {
 #pragma unroll
@@ -3129,7 +3191,7 @@ LaunchParams single_launch(const SolveParams &p)
 int z_warps(int hq)
 {
     const size_t smem = (size_t)solve_smem_z(hq, 4).total + 2048;   // + static shared memory and reserve
-    return (hq <= 17 && 4 * smem <= 228 * 1024 && 4 * tc_tmem_cols(hq) <= 512) ? 4 : 8;
+    return (hq <= 17 && 4 * smem <= 228 * 1024 && 4 * z_tmem_cols(hq) <= 512) ? 4 : 8;
 }
 
 // Kernel function, threads, dynamic shared memory and resident blocks per SM of
@@ -3183,7 +3245,7 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
                              2048 / threads);
     blocks_per_sm = std::max(blocks_per_sm, own);
     // each resident block holds its accumulator in the SM's 512 tensor-memory columns
-    if (tc) blocks_per_sm = std::min(blocks_per_sm, nw == 16 ? 2 : 512 / tc_tmem_cols(v->hq));
+    if (tc) blocks_per_sm = std::min(blocks_per_sm, nw == 16 ? 2 : 512 / (z ? z_tmem_cols(v->hq) : tc_tmem_cols(v->hq)));
     if (blocks_per_sm < 1) return fail(PRISM_ERR_UNSUPPORTED, "solve kernel does not fit on an SM (smem %zu)", smem);
     return PRISM_OK;
 }
@@ -3479,7 +3541,7 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
         float *Khi8 = nullptr, *Klo8 = nullptr, *Bz = nullptr, *Wz = nullptr;
         const Variant *zv = pick_variant(H);
         if (e == cudaSuccess && zv && tc_fits(H)) {
-            e = dev_malloc(&Bz, sizeof(float) * 2 * tc_nrows(zv->hq) * z_kd(zv->hq));
+            e = dev_malloc(&Bz, sizeof(float) * 2 * z_ndp(zv->hq) * z_kd(zv->hq));
             if (e == cudaSuccess) e = dev_malloc(&Wz, sizeof(float) * 3 * 8 * ((zv->hq + 1) / 2));
         }
         if (e == cudaSuccess && q8_capable(H)) {
