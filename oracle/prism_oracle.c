@@ -43,12 +43,11 @@
  * squares); every ADMM iteration against the dual feasibility of scaled ADMM
  * (x - xi + rho F'^T u in span(e1)) and its slack against the box projection
  * (normal-cone condition); the residuals against their definitions; the
- * PAPER fixed point against its stationarity relation.  Planted mistakes in
- * a copy of this file each fail a pin (tests/test_oracle_mutations.py).
- * PARITY UNPINNED: the factor delta/2 of the PAPER-mode multiplier step
- * (Eq. admm_dual).  No fact outside the printed formula fixes it (the fixed
- * point is the same for any positive factor), so a change of that factor
- * would pass every pin above.
+ * PAPER fixed point against its stationarity relation, and every PAPER
+ * iteration against the stationarity of its primal step combined with the
+ * multiplier step (x^{l+1} - xi + lambda^l - 2 lambda^{l+1} in span(e1), which
+ * fixes the factor delta/2 of Eq. admm_dual).  Planted mistakes in a copy of
+ * this file each fail a pin (tests/test_oracle_mutations.py).
  *
  * Residuals reported per column:
  *   primal = max( |x_1 - v0|, max_r max(0, (G x - h)_r) / ||G_r||_2 )

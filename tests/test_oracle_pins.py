@@ -422,6 +422,47 @@ def test_admm_dual_feasibility_after_every_iteration(H, dt, rho, scale):
     assert np.max(np.abs(g[1:])) <= tol(uw)
 
 
+PAPER_CASES = [(6, 0.05, 1.0, oracle.SCALE_ROWNORM), (12, 0.02, 0.4, oracle.SCALE_ROWNORM),
+               (10, 0.1, 2.5, oracle.SCALE_NONE), (20, 0.05, 0.7, oracle.SCALE_ROWNORM)]
+
+
+def _paper_state(xi, bnd, q0, v0, H, dt, L, rho, scale):
+    r = oracle.solve_batch(xi.reshape(1, H, 1), [q0], [v0], bnd.reshape(8, 1), dt, L, rho,
+                           mode=oracle.MODE_PAPER, scale=scale, want_dual_state=True)
+    return r["x"][0, :, 0], r["dual_state"][0, :, 0]
+
+
+@pytest.mark.parametrize("H,dt,rho,scale", PAPER_CASES)
+def test_paper_stationarity_after_every_iteration(H, dt, rho, scale):
+    """Eq. (admm_primal) makes x^{l+1} the minimiser of Eq. (aug_lag), with
+    lambda^l and zeta^{l+1}, subject to A x = b (x_1 = v0): its stationarity is
+        x^{l+1} - xi - lambda^l + delta G'^T (G' x^{l+1} - h' + zeta^{l+1}) in span(e1).
+    Eq. (admm_dual) moves lambda by -(delta/2) times the same G'^T (...), so the
+    last term equals 2 (lambda^l - lambda^{l+1}) and
+        x^{l+1} - xi + lambda^l - 2 lambda^{l+1} in span(e1)
+    after EVERY iteration, whatever G' is.  A multiplier step c delta with
+    c != 1/2 leaves (1/c - 2)(lambda^l - lambda^{l+1}) off e1 instead: this pins
+    the factor delta/2 of Eq. (admm_dual)."""
+    rng = np.random.default_rng(80 + H)
+    xi, bnd, q0, v0 = rand_case(rng, H, dt, tight=0.5)
+    G, _ = oracle.build_G_h(H, dt, bnd, q0, v0)
+    Gs = G / np.linalg.norm(G, axis=1)[:, None] if scale == oracle.SCALE_ROWNORM else G
+    # rounding bound of one x-step: a few ulps times the condition number of the
+    # x-step's matrix times the size of the terms
+    eps = 16 * np.finfo(float).eps * np.linalg.cond(np.eye(H) + rho * Gs.T @ Gs)
+    lam_prev = np.zeros(H)
+    moved = 0.0
+    for L in range(0, 10):
+        x1, lam1 = _paper_state(xi, bnd, q0, v0, H, dt, L + 1, rho, scale)
+        g = x1 - xi + lam_prev - 2.0 * lam1
+        tol = eps * max(1.0, float(np.max(np.abs(lam_prev))), float(np.max(np.abs(lam1))),
+                        float(np.max(np.abs(xi))), float(np.max(np.abs(x1))))
+        assert np.max(np.abs(g[1:])) <= tol, (L, np.max(np.abs(g[1:])), tol)
+        moved = max(moved, float(np.max(np.abs(lam1 - lam_prev))))
+        lam_prev = lam1
+    assert eps < 1e-5 and moved > 1e3 * eps   # a wrong factor would be far outside the bound
+
+
 @pytest.mark.parametrize("H,dt,rho,scale", ADMM_CASES)
 def test_admm_slack_step_is_the_box_projection(H, dt, rho, scale):
     """The slack of iteration l is z^l = u^{l-1} + F'x^l - u^l (the multiplier
