@@ -3864,20 +3864,19 @@ prism_status prism_proj_solve_host(prism_proj_t h, int batch, const float *q0_ho
     float *d_v0 = d_q0 + h->J;
     float *pr = primal_res_host ? (pr_m ? pr_m : d_pr) : nullptr;
     float *du = dual_res_host ? (du_m ? du_m : d_du) : nullptr;
-    {
-        // every argument error is reported before anything is enqueued
-        SolveParams chk;
-        st = prepare_solve(h, batch, d_q0, d_v0, d_x, iters, rho, d_x, chk);
-        if (st) return st;
-    }
+    // every argument error is reported before anything is enqueued
+    SolveParams chk;
+    st = prepare_solve(h, batch, d_q0, d_v0, d_x, iters, rho, d_x, chk);
+    if (st) return st;
     CUDA_TRY(cudaMemcpyAsync(d_q0, q0_host, sizeof(float) * h->J, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(d_v0, v0_host, sizeof(float) * h->J, cudaMemcpyHostToDevice, s));
     if (chunks > 1) {
         st = host_pipeline_init(h);
-        if (st) return st;
-        SolveParams p0;
-        prepare_solve(h, batch, d_q0, d_v0, d_x, iters, rho, d_x, p0);
-        const int cs = host_chunk_samples(batch, h->J, p0.flat, chunks);
+        if (st) {
+            cudaStreamSynchronize(s);   // the q0 / v0 copies read host memory
+            return st;
+        }
+        const int cs = host_chunk_samples(batch, h->J, chk.flat, chunks);
         const int nch = (batch + cs - 1) / cs;
         cudaEvent_t *ev_in = h->hp_ev, *ev_k = h->hp_ev + PRISM_HOST_MAX_CHUNKS;
         cudaEvent_t ev_start = h->hp_ev[2 * PRISM_HOST_MAX_CHUNKS], ev_end = h->hp_ev[2 * PRISM_HOST_MAX_CHUNKS + 1];
