@@ -32,7 +32,7 @@ WORKLOAD = workloads.WORKLOADS["realistic"]
 METRIC = "projected trajectories/s"
 UNIT = "trajectories/s"
 N_INPUTS = 64
-PRECS = {"fp32": 0, "tf32x3": 3}
+PRECS = {"fp32": 0, "tf32x3": 3, "bf16x3": 1}
 
 # DRAM bytes (read + write) of one launch of the solve kernel on this workload,
 # from one ncu capture of that launch, keyed by the hash of the code (comments
@@ -499,7 +499,7 @@ def run_precision(args):
     o = oracle.solve_batch(b["xi"][:NS], b["q0"], b["v0"], b["bounds"], w.dt, total, 1.0,
                            nthreads=os.cpu_count() or 1)
     oracle_s = time.perf_counter() - t0
-    variants = [("fp32", pp.PREC_FP32, 0), ("tf32x3", pp.PREC_TF32X3, 0),
+    variants = [("fp32", pp.PREC_FP32, 0), ("tf32x3", pp.PREC_TF32X3, 0), ("bf16x3", pp.PREC_BF16X3, 0),
                 ("tf32+polish20", pp.PREC_TF32, polish), ("tf32+polish100", pp.PREC_TF32, 100),
                 ("tf32 (no polish)", pp.PREC_TF32, 0)]
     res = {}
@@ -1016,6 +1016,8 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": measured_traffic(args.prec),
                 "kernel": ("solve_kernel (persistent ADMM, K-apply on the FP32 pipe)" if args.prec == "fp32"
+                           else "solve_kernel (persistent ADMM, K-apply bf16x3 on the tensor cores)"
+                           if args.prec == "bf16x3"
                            else f"solve_kernel_z (persistent ADMM, paired-FP32 rows, K-apply {args.prec})"),
                 "peak_basis": f"FP32 FMA issue rate {q['num_sms']} SMs x 128 lanes x 2 flop x 2032 MHz"
                               " (max SM clock; derived, no measured FP32 peak)",
@@ -1035,6 +1037,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.prec == "fp32" else
+                         "f32 (K-apply on tensor cores as sums of three-way split-bf16 products, f32 accumulate)"
+                         if args.prec == "bf16x3" else
                          "f32 (K-apply on tensor cores as exact sums of split-tf32 products, f32 accumulate)",
                 "data": "synthetic (seeded white-noise samples; no dataset)",
                 "config": config_dict(),

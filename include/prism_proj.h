@@ -82,8 +82,13 @@ enum { PRISM_SCALE_ROWNORM = 0, PRISM_SCALE_NONE = 1 };
  * both operands split into a tf32 high part and a remainder (products of all
  * parts, FP32 accumulation: FP32-level accuracy); TF32 on the tensor cores with
  * the high parts only, except for the last polish_iters iterations
- * (prism_solve_opts), which use the split.  BF16X3 is reserved and returns
- * PRISM_ERR_UNSUPPORTED in this build. */
+ * (prism_solve_opts), which use the split.  BF16X3 on the tensor cores in
+ * bf16 (kind::f16 MMAs): both operands split into three bf16 parts, all
+ * products but the one of the two smallest parts, FP32 accumulation
+ * (FP32-level accuracy); ADMM mode, single solves (prism_proj_solve,
+ * prism_proj_solve_ex, prism_proj_sample_solve, prism_proj_solve_host) only:
+ * PAPER mode fails at factor and plans fail at create with
+ * PRISM_ERR_UNSUPPORTED. */
 enum { PRISM_PREC_FP32 = 0, PRISM_PREC_BF16X3 = 1, PRISM_PREC_TF32 = 2, PRISM_PREC_TF32X3 = 3 };
 
 #define PRISM_MAX_H 132   /* horizon limit of the on-chip solve kernel          */
@@ -115,8 +120,8 @@ prism_status prism_proj_create(int J, int H, double dt,
  *   and kb = [M^-1]_{1:H,H+1} on the device (FP64, plus an FP32 copy used by
  *   the solve).  rho > 0 is the paper's penalty delta.  prec selects the
  *   K-apply of prism_proj_solve: PRISM_PREC_FP32 (FP32 pipe, any H) or
- *   PRISM_PREC_TF32X3 / PRISM_PREC_TF32 (tensor cores, H <= 116; larger H
- *   returns PRISM_ERR_UNSUPPORTED).  Enqueued on
+ *   PRISM_PREC_TF32X3 / PRISM_PREC_TF32 / PRISM_PREC_BF16X3 (tensor cores,
+ *   H <= 116; larger H returns PRISM_ERR_UNSUPPORTED).  Enqueued on
  *   cuda_stream; re-factoring a handle replaces its factor (the caller orders
  *   it after solves that still use the old one).
  */

@@ -192,7 +192,7 @@ struct prism_proj_s {
     struct LaunchCache {
         bool valid = false;
         int mode = -1, nw = -1;
-        bool tc = false;
+        bool tc = false, bf = false;
         const void *fn = nullptr;        // the kernel (a solve_fn)
         int threads = 0, bps = 0;
         size_t smem = 0;
@@ -766,6 +766,45 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t 
                  :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// ---- three-way bf16 split (PRISM_PREC_BF16X3).  A float v is carried as three
+// bf16 parts h + m + l: h the bf16 nearest v, m the bf16 nearest v - h, l the
+// bf16 nearest v - h - m (both remainders are exact in FP32), so the parts
+// reproduce v to about 2^-27 |v|.  A bf16 operand is K-major without swizzle
+// like the tf32 ones, with 8 elements of K per 16-byte core-matrix row: element
+// (r, k) of an R x KT matrix at byte ((r/8)(KT/8) + k/8) 128 + (r%8) 16 + (k%8) 2.
+__host__ __device__ __forceinline__ int cm_off16(int r, int k, int KT)
+{
+    return ((r >> 3) * (KT >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ uint16_t bf16_rn_bits(float v)
+{
+    uint16_t r;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ void bf16_split3(float v, uint16_t &h, uint16_t &m, uint16_t &l)
+{
+    h = bf16_rn_bits(v);
+    const float r1 = v - __uint_as_float((uint32_t)h << 16);
+    m = bf16_rn_bits(r1);
+    l = bf16_rn_bits(r1 - __uint_as_float((uint32_t)m << 16));
+}
+
 // Programmatic dependent launch: the grid launched after this one on the stream
 // with programmatic serialisation may start once every block of this one has
 // executed this (or exited).  No-op without a dependent launch.
@@ -949,7 +988,13 @@ __device__ __forceinline__ void normals4(unsigned long long q, unsigned long lon
 // high parts over low parts) and keeps D (128 x 2 ND fp32) in tensor memory.
 // One M = 128 MMA per K-step gives K' rhs + kb' v0 as the sum of a column's two
 // rows in both halves of D: the products of the two tf32 parts of both
-// operands, i.e. FP32-level accuracy.
+// operands, i.e. FP32-level accuracy.  BF = the same regions as bf16 with the K
+// extent doubled (PRISM_PREC_BF16X3): a column's rhs = h + m + l, [K' | kb'] =
+// H + M + L (bf16_split3); A holds h over m in K segment 0 and l over 0 in
+// segment 1, B holds H over M in segment 0 and L over 0 in segment 1, and three
+// passes of kind::f16 MMAs (A0 B0, A0 B1, A1 B0) leave in D's two rows and two
+// halves, summed by the same readback, (h+m)(H+M) + (h+m)L + l(H+M): every
+// product of the parts but l L (about 2^-36 of the product).
 // ===========================================================================
 template <int HQ>
 __host__ __device__ constexpr int solve_min_blocks() { return HQ <= 17 ? 2 : 1; }
@@ -982,10 +1027,11 @@ __host__ __device__ inline SolveSmem solve_smem(int hq, int n, int MP, bool tc)
     return L;
 }
 
-template <int HQ, int MODE, bool TC, bool BATCHED>
+template <int HQ, int MODE, bool TC, bool BATCHED, bool BF = false>
 __global__ void __launch_bounds__(NTHREADS, solve_min_blocks<HQ>())
 solve_kernel(const __grid_constant__ LaunchParams P)
 {
+    static_assert(!BF || TC, "the bf16 split is a tensor-core K-apply");
     constexpr int HP = 4 * HQ;
     constexpr int CP = col_stride(HQ);
     constexpr int TMEM_COLS = tc_tmem_cols(HQ);
@@ -1077,7 +1123,35 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 was[e] = (e < H) ? (e == 0 ? p.wa0 : p.wa) : 0.0f;
                 wjs[e] = (e >= 1 && e < H) ? (e == 1 ? p.wj0 : p.wj) : 0.0f;
             }
-            if (TC) {
+            if (TC && BF) {
+                // B in bf16: segment 0 (K indices [0, KD)) holds the H parts over the
+                // M parts, segment 1 ([KD, 2 KD)) the L parts over zero rows; the
+                // rows, K slots and membership exactly as in the tf32 layout below
+                uint16_t *Bs = reinterpret_cast<uint16_t *>(smem_raw + L.bhi);
+                constexpr int HQ4 = tc_hq4(HQ);
+                for (int e = tid; e < ND * KD; e += NTHREADS) {
+                    const int pc = e / KD, kq = e - pc * KD;
+                    const int xt = (pc & 3) * HQ + (pc >> 2);
+                    const bool prefix = pc >= 4 * HQ;
+                    const int i = prefix ? n + (pc & 3) : xt - 1;
+                    const int kb_ = kq / HQ4, kr = kq - kb_ * HQ4;
+                    const int rr = (kr & ~3) | ((kr & 3) ^ kb_);
+                    const int xk = kb_ * HQ + rr;
+                    const bool v0col = kq == HQ;
+                    const int j = v0col ? n : xk - 1;
+                    const bool in = (prefix || (xt >= 1 && xt <= n)) && (v0col || (rr < HQ && xk >= 1 && xk <= n));
+                    const int src = i * (n + 4) + j;
+                    uint16_t bh = 0, bm = 0, bl = 0;
+                    if (in) bf16_split3(p.Khi[src] + p.Klo[src], bh, bm, bl);
+                    Bs[cm_off16(pc, kq, 2 * KD) >> 1] = bh;
+                    Bs[cm_off16(pc + ND, kq, 2 * KD) >> 1] = bm;
+                    Bs[cm_off16(pc, KD + kq, 2 * KD) >> 1] = bl;
+                    Bs[cm_off16(pc + ND, KD + kq, 2 * KD) >> 1] = 0;
+                }
+                // A zeroed (same bytes as the tf32 layout): padding K slots and the
+                // rows below l in segment 1 stay zero
+                for (int e = tid; e < 128 * KD; e += NTHREADS) reinterpret_cast<float *>(As)[e] = 0.0f;
+            } else if (TC) {
                 // B = [K' | kb'] (rows = D columns in the interleaved output order,
                 // reduction j) split in tf32 high / low parts; A zeroed (its padding
                 // columns k > n must stay zero).
@@ -1164,7 +1238,14 @@ solve_kernel(const __grid_constant__ LaunchParams P)
         __syncthreads();
         if (b == 0) {
             xs[2 * CP + c] = colv ? v0j : 0.0f;
-            if (TC) {
+            if (TC && BF) {
+                const float v = colv ? v0j : 0.0f;
+                uint16_t h, m, l;
+                bf16_split3(v, h, m, l);
+                *reinterpret_cast<uint16_t *>(As + cm_off16(arow_hi, HQ, 2 * KD)) = h;
+                *reinterpret_cast<uint16_t *>(As + cm_off16(arow_lo, HQ, 2 * KD)) = m;
+                *reinterpret_cast<uint16_t *>(As + cm_off16(arow_hi, KD + HQ, 2 * KD)) = l;
+            } else if (TC) {
                 // K slot HQ of A: v0 of this column, split like the right-hand sides
                 const float v = colv ? v0j : 0.0f;
                 const float hi = tf32_rna(v);
@@ -1337,17 +1418,36 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 // the four quarter-threads of a column on different banks).  Rows
                 // that are not right-hand-side rows (x_0, padding) meet zero columns
                 // of B.  Iterations before the polish phase use the high parts only.
-                const bool split = l >= iters - polish;
-                float *ahi = reinterpret_cast<float *>(As + cm_off(arow_hi, tc_hq4(HQ) * b, KD));
-                constexpr int LO = 8 * KD;   // floats from a column's high row to its low row
-                float *aw[4];
+                const bool split = BF || l >= iters - polish;
+                if (BF) {
+                    // the same K slots in bf16: h and m in the column's two rows of
+                    // segment 0, l in its first row of segment 1
+                    unsigned char *arow = As + cm_off16(arow_hi, 0, 2 * KD);
+                    constexpr int LO16 = 2 * KD * 16;   // bytes from row arow_hi to arow_hi + 8
+                    constexpr int SEG = KD * 16;        // bytes from K index k to k + KD
+                    const int kb0 = tc_hq4(HQ) * b;
 #pragma unroll
-                for (int m = 0; m < 4; ++m) aw[m] = ahi + (m ^ b);
+                    for (int r = 0; r < HQ; ++r) {
+                        const int k = kb0 + 4 * (r >> 2) + ((r & 3) ^ b);
+                        uint16_t *a = reinterpret_cast<uint16_t *>(arow + (k >> 3) * 128 + (k & 7) * 2);
+                        uint16_t h, m, lo;
+                        bf16_split3(rv[r], h, m, lo);
+                        a[0] = h;
+                        a[LO16 / 2] = m;
+                        a[SEG / 2] = lo;
+                    }
+                } else {
+                    float *ahi = reinterpret_cast<float *>(As + cm_off(arow_hi, tc_hq4(HQ) * b, KD));
+                    constexpr int LO = 8 * KD;   // floats from a column's high row to its low row
+                    float *aw[4];
 #pragma unroll
-                for (int r = 0; r < HQ; ++r) {
-                    const float hi = tf32_rna(rv[r]);
-                    aw[r & 3][32 * (r >> 2)] = hi;
-                    if (split) aw[r & 3][32 * (r >> 2) + LO] = rv[r] - hi;
+                    for (int m = 0; m < 4; ++m) aw[m] = ahi + (m ^ b);
+#pragma unroll
+                    for (int r = 0; r < HQ; ++r) {
+                        const float hi = tf32_rna(rv[r]);
+                        aw[r & 3][32 * (r >> 2)] = hi;
+                        if (split) aw[r & 3][32 * (r >> 2) + LO] = rv[r] - hi;
+                    }
                 }
                 // A visible to the tensor core, the previous readback of D finished;
                 // a warp whose MMA wait ran out stops the block here
@@ -1362,7 +1462,28 @@ solve_kernel(const __grid_constant__ LaunchParams P)
                 // rows and the v0 column, B = [K' | kb'] high parts (columns < ND, in
                 // the interleaved output order) stacked over its low parts (columns
                 // >= ND; only in the polish phase)
-                if (warp == 0) {
+                if (BF && warp == 0) {
+                    // K-major bf16, 2 KD elements per row: a K-step of 16 elements is
+                    // two core matrices (16 descriptor units), a segment KD units
+                    const uint32_t idesc = umma_idesc_bf16(128, 2 * ND);
+                    const uint32_t sbo = (uint32_t)(2 * KD >> 3) * 128u;
+                    const uint64_t da = umma_desc(smem_addr(As), 128u, sbo);
+                    const uint64_t db = umma_desc(smem_addr(smem_raw + L.bhi), 128u, sbo);
+                    if (elect_one()) {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                        for (int pass = 0; pass < 3; ++pass) {
+                            const uint64_t ao = (pass == 2) ? (uint64_t)KD : 0u;   // A segment 1 on the last pass
+                            const uint64_t bo = (pass == 1) ? (uint64_t)KD : 0u;   // B segment 1 on the second
+                            for (int ks = 0; ks < (KD >> 4); ++ks) {
+                                const uint64_t kk = (uint64_t)(16 * ks);
+                                umma_f16(tbase, da + ao + kk, db + bo + kk, idesc, (pass > 0 || ks > 0) ? 1u : 0u);
+                            }
+                        }
+                        umma_commit(smem_addr(&mma_bar));
+                    }
+                    __syncwarp();
+                } else if (warp == 0) {
                     // descriptors formed by the whole warp (uniform), one elected lane
                     // issues (measured: about 25 % less issue time than forming them in
                     // a single thread)
@@ -3046,10 +3167,11 @@ struct Variant {
     // the ADMM tensor-core kernels that read warm-start inputs (x_init, dual_init);
     // the ones above do not (fewer registers)
     solve_fn admm_tc_w, b_admm_tc_w, admm_tc4_w, b_admm_tc4_w;
+    solve_fn admm_bf;   // ADMM with the three-way bf16 split K-apply (one problem per launch)
 };
 
 // The ADMM iteration with the tensor-core K-apply runs on solve_kernel_z; every
-// other combination on solve_kernel.
+// other combination (the bf16 split included) on solve_kernel.
 #define VARIANT(HQv)                                                                                    \
     {HQv, solve_kernel<HQv, PRISM_MODE_ADMM, false, false>, solve_kernel<HQv, PRISM_MODE_PAPER, false, false>, \
      solve_kernel_z<HQv, 8, false, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false>,                  \
@@ -3057,7 +3179,8 @@ struct Variant {
      solve_kernel_z<HQv, 8, true, false>, solve_kernel<HQv, PRISM_MODE_PAPER, true, true>,                    \
      solve_kernel_z<HQv, 4, false, false>, solve_kernel_z<HQv, 4, true, false>,                               \
      solve_kernel_z<HQv, 8, false, true>, solve_kernel_z<HQv, 8, true, true>,                                 \
-     solve_kernel_z<HQv, 4, false, true>, solve_kernel_z<HQv, 4, true, true>}
+     solve_kernel_z<HQv, 4, false, true>, solve_kernel_z<HQv, 4, true, true>,                                 \
+     solve_kernel<HQv, PRISM_MODE_ADMM, true, false, true>}
 // prev_variant_hq (used for the rows that always exist) must list the same chunks.
 constexpr int kVariantHQ[] = {3, 5, 7, 9, 11, 13, 15, 17, 21, 25, 29, 33};
 constexpr bool variant_chain_ok()
@@ -3198,12 +3321,15 @@ int z_warps(int hq)
 // one solve-kernel variant.  nw: warps of solve_kernel_z (ADMM on the tensor
 // cores; 0 = z_warps), ignored by the other kernels.
 prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, int MP_max, int device, int nw,
-                            solve_fn &fn, int &threads, size_t &smem, int &blocks_per_sm, int &hq, bool warm)
+                            solve_fn &fn, int &threads, size_t &smem, int &blocks_per_sm, int &hq, bool warm,
+                            bool bf = false)
 {
     const Variant *v = pick_variant(H);
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", H);
     hq = v->hq;
-    const bool z = tc && mode == PRISM_MODE_ADMM;
+    if (bf && (batched || mode != PRISM_MODE_ADMM || !tc))
+        return fail(PRISM_ERR_UNSUPPORTED, "the bf16 split K-apply runs ADMM solves of one problem per launch");
+    const bool z = tc && mode == PRISM_MODE_ADMM && !bf;
     if (z && nw == 0) nw = z_warps(v->hq);
     if (!z) nw = 8;
     if (nw == 16) {
@@ -3214,6 +3340,8 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
         fn = (hq8 == 9) ? (batched ? solve_kernel_q8<9, true> : solve_kernel_q8<9, false>)
                         : (batched ? solve_kernel_q8<13, true> : solve_kernel_q8<13, false>);
         smem = (size_t)solve_smem_q8(hq8).total;
+    } else if (bf) {
+        fn = v->admm_bf;
     } else if (!batched) {
         fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? (warm ? v->admm_tc4_w : v->admm_tc4)
                                                         : (warm ? v->admm_tc_w : v->admm_tc))
@@ -3255,10 +3383,11 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
 {
     v = pick_variant(h->H);
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", h->H);
-    const bool tc = h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32;
-    const int nw = (tc && h->mode == PRISM_MODE_ADMM) ? handle_warps(h) : 0;
+    const bool bf = h->prec == PRISM_PREC_BF16X3;
+    const bool tc = h->prec == PRISM_PREC_TF32X3 || h->prec == PRISM_PREC_TF32 || bf;
+    const int nw = (tc && !bf && h->mode == PRISM_MODE_ADMM) ? handle_warps(h) : 0;
     prism_proj_s::LaunchCache &c = h->lc[warm ? 1 : 0];
-    if (c.valid && c.mode == h->mode && c.tc == tc && c.nw == nw) {
+    if (c.valid && c.mode == h->mode && c.tc == tc && c.bf == bf && c.nw == nw) {
         fn = reinterpret_cast<solve_fn>(const_cast<void *>(c.fn));
         threads = c.threads;
         smem = c.smem;
@@ -3266,18 +3395,19 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
     } else {
         int hq;
         prism_status st = variant_config(h->H, h->mode, tc, false, h->n, h->MP, h->device, nw, fn, threads, smem,
-                                         blocks_per_sm, hq, warm);
+                                         blocks_per_sm, hq, warm, bf);
         if (st) return st;
         c.valid = true;
         c.mode = h->mode;
         c.tc = tc;
+        c.bf = bf;
         c.nw = nw;
         c.fn = reinterpret_cast<const void *>(fn);
         c.threads = threads;
         c.smem = smem;
         c.bps = blocks_per_sm;
     }
-    const bool z = tc && h->mode == PRISM_MODE_ADMM;
+    const bool z = tc && !bf && h->mode == PRISM_MODE_ADMM;
     const int ntiles = solve_ntiles(batch, h->J, z ? (threads == 512 ? 64 : threads / 4) : 0);
     grid = std::max(1, std::min(ntiles, blocks_per_sm * h->num_sms));
     return PRISM_OK;
@@ -3516,9 +3646,9 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
     if (prec != PRISM_PREC_FP32 && prec != PRISM_PREC_BF16X3 && prec != PRISM_PREC_TF32 &&
         prec != PRISM_PREC_TF32X3)
         return fail(PRISM_ERR_INVALID_ARG, "bad precision %d", prec);
-    if (prec == PRISM_PREC_BF16X3)
-        return fail(PRISM_ERR_UNSUPPORTED, "precision %d is not built", prec);
-    if ((prec == PRISM_PREC_TF32X3 || prec == PRISM_PREC_TF32) && !tc_fits(h->H))
+    if (prec == PRISM_PREC_BF16X3 && mode != PRISM_MODE_ADMM)
+        return fail(PRISM_ERR_UNSUPPORTED, "the bf16 split K-apply is built for the ADMM iteration only");
+    if ((prec == PRISM_PREC_TF32X3 || prec == PRISM_PREC_TF32 || prec == PRISM_PREC_BF16X3) && !tc_fits(h->H))
         return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the tensor-core kernel limit", h->H);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int H = h->H, n = h->n, MP = h->MP;
@@ -4090,6 +4220,10 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
         st = prepare_solve(q.h, q.batch, q.q0, q.v0, q.samples, iters, q.h->rho, q.out, all[k]);
         if (st) break;
         if (q.h->device != dev) { st = fail(PRISM_ERR_INVALID_ARG, "problem %d: handle on another device", k); break; }
+        if (q.h->prec == PRISM_PREC_BF16X3) {
+            st = fail(PRISM_ERR_UNSUPPORTED, "problem %d: plans do not run the bf16 split K-apply", k);
+            break;
+        }
         all[k].primal = q.primal_res;
         all[k].dual = q.dual_res;
         all[k].x_init = q.x_init;

@@ -300,7 +300,7 @@ def test_errors_are_reported_not_raised_on_device():
         P.solve(q0, v0, xi, 10, rho=2.0)
     assert e.value.status == 3
     with pytest.raises(pp.PrismError) as e:
-        P.factor(1.0, prec=pp.PREC_BF16X3)
+        P.factor(1.0, pp.MODE_PAPER, pp.SCALE_ROWNORM, pp.PREC_BF16X3)
     assert e.value.status == 7
     P.factor(1.0)
     with pytest.raises(pp.PrismError) as e:
