@@ -42,17 +42,21 @@ PRECS = {"fp32": 0, "tf32x3": 3, "bf16x3": 1}
 # ncu pipe utilisation of the same launch (sm__pipe_*_cycles_active and issue
 # activity, % of peak sustained), keyed like MEASURED_TRAFFIC.
 MEASURED_PIPES = {
-    "tf32x3": {"kernel_source_sha256_16": "55b040e9dd7bbbcf", "issue_active_pct": 59.5,
+    "tf32x3": {"kernel_source_sha256_16": "10e87e4db58d6965", "issue_active_pct": 59.4,
                "sm__pipe_tensor_cycles_active_pct": 39.4, "sm__pipe_fma_cycles_active_pct": 38.6,
                "sm__inst_executed_pipe_alu_pct": 39.5},
-    "fp32": {"kernel_source_sha256_16": "55b040e9dd7bbbcf", "issue_active_pct": 61.6,
+    "fp32": {"kernel_source_sha256_16": "10e87e4db58d6965", "issue_active_pct": 61.6,
              "sm__pipe_tensor_cycles_active_pct": 0.0, "sm__pipe_fma_cycles_active_pct": 43.3,
              "sm__inst_executed_pipe_alu_pct": 20.1},
+    "bf16x3": {"kernel_source_sha256_16": "10e87e4db58d6965", "issue_active_pct": 63.7,
+               "sm__pipe_tensor_cycles_active_pct": 24.1, "sm__pipe_fma_cycles_active_pct": 33.7,
+               "sm__inst_executed_pipe_alu_pct": 36.0},
 }
 
 MEASURED_TRAFFIC = {
-    "fp32": {"kernel_source_sha256_16": "55b040e9dd7bbbcf", "bytes": 9919488},
-    "tf32x3": {"kernel_source_sha256_16": "55b040e9dd7bbbcf", "bytes": 9936640},
+    "fp32": {"kernel_source_sha256_16": "10e87e4db58d6965", "bytes": 9919232},
+    "tf32x3": {"kernel_source_sha256_16": "10e87e4db58d6965", "bytes": 9936640},
+    "bf16x3": {"kernel_source_sha256_16": "10e87e4db58d6965", "bytes": 9938176},
 }
 
 
@@ -111,21 +115,25 @@ def flops_per_column_iteration(H: int) -> int:
 
 
 def pipe_rooflines(flops_total: float, flops_kapply: float, seconds: float, num_sms: int, peaks: dict,
-                   counters=None) -> dict:
+                   counters=None, operand: str = "tf32") -> dict:
     """Per-pipe roofline of one launch: the stencil, clip and multiplier work
     (everything but the K-apply) against the FP32 issue rate, the K-apply against
-    the tf32 tensor rate (half the measured bf16 rate).  counters: ncu pipe
-    utilisations of the same kernel, or None."""
+    the tensor rate of its operand type (tf32: half the measured bf16 rate; bf16:
+    the measured bf16 rate).  counters: ncu pipe utilisations of the same kernel,
+    or None."""
     simt = flops_total - flops_kapply
     p_simt = peak_fp32_tflops(num_sms, 2032.0)
     bf16 = peaks.get("bf16_tflops")
-    p_tc = 0.5 * bf16 if bf16 else None
+    ratio = 1.0 if operand == "bf16" else 0.5
+    p_tc = ratio * bf16 if bf16 else None
     out = {"simt": {"achieved": simt / seconds / 1e12, "peak": p_simt, "unit": "TFLOP/s",
                     "frac": simt / seconds / 1e12 / p_simt,
                     "peak_basis": "FP32 FMA issue rate, 2032 MHz (derived)"},
            "tensor": {"achieved": flops_kapply / seconds / 1e12, "peak": p_tc, "unit": "TFLOP/s",
                       "frac": (flops_kapply / seconds / 1e12 / p_tc) if p_tc else None,
-                      "peak_basis": "tf32 dense = 0.5 x measured bf16 burst (%s TFLOP/s, of measured)" % bf16}}
+                      "peak_basis": ("bf16 dense = measured bf16 burst (%s TFLOP/s, of measured)" % bf16
+                                     if operand == "bf16" else
+                                     "tf32 dense = 0.5 x measured bf16 burst (%s TFLOP/s, of measured)" % bf16)}}
     if counters:
         out["ncu"] = counters
     return out
@@ -1025,7 +1033,7 @@ def main():
                 "algorithmic_bytes_per_launch": 2 * w.N * w.H * w.J * 4 + 2 * w.N * w.J * 4}
     kflops = w.N * w.J * w.iters * kapply_flops_per_column_iteration(w.H) if args.prec != "fp32" else 0
     roofline_pipes = pipe_rooflines(flops, kflops, avg_launch_s, q["num_sms"], load_peaks(),
-                                    measured_pipes(args.prec))
+                                    measured_pipes(args.prec), "bf16" if args.prec == "bf16x3" else "tf32")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

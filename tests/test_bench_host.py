@@ -48,3 +48,6 @@ def test_pipe_rooflines_split_the_work_between_the_pipes():
     assert abs(r["tensor"]["frac"] - kap * 1e-3 / 900.0) < 1e-12
     assert "ncu" not in r
     assert b.pipe_rooflines(1.0, 0.0, 1.0, 148, {})["tensor"]["frac"] is None
+    # the bf16 split K-apply is measured against the bf16 rate itself
+    rb = b.pipe_rooflines(total * 1e9, kap * 1e9, 1.0, 148, {"bf16_tflops": 1800.0}, operand="bf16")
+    assert abs(rb["tensor"]["peak"] - 1800.0) < 1e-9
