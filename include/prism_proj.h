@@ -83,8 +83,8 @@ enum { PRISM_SCALE_ROWNORM = 0, PRISM_SCALE_NONE = 1 };
  * parts, FP32 accumulation: FP32-level accuracy); TF32 on the tensor cores with
  * the high parts only, except for the last polish_iters iterations
  * (prism_solve_opts), which use the split.  BF16X3 on the tensor cores in
- * bf16 (kind::f16 MMAs): both operands split into three bf16 parts, all
- * products but the one of the two smallest parts, FP32 accumulation
+ * bf16 (kind::f16 MMAs): both operands split exactly into three bf16 parts,
+ * all products but the one of the two smallest parts, FP32 accumulation
  * (FP32-level accuracy); ADMM mode, single solves (prism_proj_solve,
  * prism_proj_solve_ex, prism_proj_sample_solve, prism_proj_solve_host) only:
  * PAPER mode fails at factor and plans fail at create with

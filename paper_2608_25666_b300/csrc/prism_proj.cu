@@ -768,8 +768,9 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t 
 
 // ---- three-way bf16 split (PRISM_PREC_BF16X3).  A float v is carried as three
 // bf16 parts h + m + l: h the bf16 nearest v, m the bf16 nearest v - h, l the
-// bf16 nearest v - h - m (both remainders are exact in FP32), so the parts
-// reproduce v to about 2^-27 |v|.  A bf16 operand is K-major without swizzle
+// bf16 nearest v - h - m.  Both remainders are exact in FP32, and each part takes
+// the next 8 of v's 24 significant bits, so for normal floats h + m + l = v
+// exactly (l is v - h - m itself, |l| <= 2^-16 |v|).  A bf16 operand is K-major without swizzle
 // like the tf32 ones, with 8 elements of K per 16-byte core-matrix row: element
 // (r, k) of an R x KT matrix at byte ((r/8)(KT/8) + k/8) 128 + (r%8) 16 + (k%8) 2.
 __host__ __device__ __forceinline__ int cm_off16(int r, int k, int KT)
@@ -994,7 +995,8 @@ __device__ __forceinline__ void normals4(unsigned long long q, unsigned long lon
 // segment 1, B holds H over M in segment 0 and L over 0 in segment 1, and three
 // passes of kind::f16 MMAs (A0 B0, A0 B1, A1 B0) leave in D's two rows and two
 // halves, summed by the same readback, (h+m)(H+M) + (h+m)L + l(H+M): every
-// product of the parts but l L (about 2^-36 of the product).
+// product of the parts but l L (at most 2^-32 of the product); each partial
+// product of two bf16 values is exact in FP32.
 // ===========================================================================
 template <int HQ>
 __host__ __device__ constexpr int solve_min_blocks() { return HQ <= 17 ? 2 : 1; }
