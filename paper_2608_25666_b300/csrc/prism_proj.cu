@@ -3169,7 +3169,7 @@ struct Variant {
     // the ADMM tensor-core kernels that read warm-start inputs (x_init, dual_init);
     // the ones above do not (fewer registers)
     solve_fn admm_tc_w, b_admm_tc_w, admm_tc4_w, b_admm_tc4_w;
-    solve_fn admm_bf;   // ADMM with the three-way bf16 split K-apply (one problem per launch)
+    solve_fn admm_bf, paper_bf;   // the three-way bf16 split K-apply (one problem per launch)
 };
 
 // The ADMM iteration with the tensor-core K-apply runs on solve_kernel_z; every
@@ -3182,7 +3182,7 @@ struct Variant {
      solve_kernel_z<HQv, 4, false, false>, solve_kernel_z<HQv, 4, true, false>,                               \
      solve_kernel_z<HQv, 8, false, true>, solve_kernel_z<HQv, 8, true, true>,                                 \
      solve_kernel_z<HQv, 4, false, true>, solve_kernel_z<HQv, 4, true, true>,                                 \
-     solve_kernel<HQv, PRISM_MODE_ADMM, true, false, true>}
+     solve_kernel<HQv, PRISM_MODE_ADMM, true, false, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false, true>}
 // prev_variant_hq (used for the rows that always exist) must list the same chunks.
 constexpr int kVariantHQ[] = {3, 5, 7, 9, 11, 13, 15, 17, 21, 25, 29, 33};
 constexpr bool variant_chain_ok()
@@ -3329,8 +3329,8 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
     const Variant *v = pick_variant(H);
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", H);
     hq = v->hq;
-    if (bf && (batched || mode != PRISM_MODE_ADMM || !tc))
-        return fail(PRISM_ERR_UNSUPPORTED, "the bf16 split K-apply runs ADMM solves of one problem per launch");
+    if (bf && (batched || !tc))
+        return fail(PRISM_ERR_UNSUPPORTED, "the bf16 split K-apply runs solves of one problem per launch");
     const bool z = tc && mode == PRISM_MODE_ADMM && !bf;
     if (z && nw == 0) nw = z_warps(v->hq);
     if (!z) nw = 8;
@@ -3343,7 +3343,7 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
                         : (batched ? solve_kernel_q8<13, true> : solve_kernel_q8<13, false>);
         smem = (size_t)solve_smem_q8(hq8).total;
     } else if (bf) {
-        fn = v->admm_bf;
+        fn = (mode == PRISM_MODE_ADMM) ? v->admm_bf : v->paper_bf;
     } else if (!batched) {
         fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? (warm ? v->admm_tc4_w : v->admm_tc4)
                                                         : (warm ? v->admm_tc_w : v->admm_tc))
@@ -3648,8 +3648,6 @@ prism_status prism_proj_factor(prism_proj_t h, double rho, int mode, int scale, 
     if (prec != PRISM_PREC_FP32 && prec != PRISM_PREC_BF16X3 && prec != PRISM_PREC_TF32 &&
         prec != PRISM_PREC_TF32X3)
         return fail(PRISM_ERR_INVALID_ARG, "bad precision %d", prec);
-    if (prec == PRISM_PREC_BF16X3 && mode != PRISM_MODE_ADMM)
-        return fail(PRISM_ERR_UNSUPPORTED, "the bf16 split K-apply is built for the ADMM iteration only");
     if ((prec == PRISM_PREC_TF32X3 || prec == PRISM_PREC_TF32 || prec == PRISM_PREC_BF16X3) && !tc_fits(h->H))
         return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the tensor-core kernel limit", h->H);
     cudaStream_t s = (cudaStream_t)cuda_stream;

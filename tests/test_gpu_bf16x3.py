@@ -115,16 +115,31 @@ def test_bf16x3_warm_start_sampling_and_host_buffers():
     P.close()
 
 
-def test_bf16x3_unsupported_combinations():
-    """PAPER mode with the bf16 split fails at factor, a plan with such a handle
-    fails at create (PRISM_ERR_UNSUPPORTED), and the handle still solves."""
+@pytest.mark.parametrize("N,J,H,dt,iters", [(1, 1, 2, 0.05, 50), (7, 5, 17, 0.02, 60), (20, 7, 45, 0.01, 80),
+                                         (13, 14, 64, 0.02, 50), (3, 2, 101, 0.02, 40)])
+def test_bf16x3_paper_mode(N, J, H, dt, iters):
+    """The printed iteration (PAPER mode) with the bf16 split K-apply."""
+    b = workloads.make_custom(99 + H, N, J, H, dt, scale=0.8)
+    g = gpu_solve(b, iters, 0.7, mode=pp.MODE_PAPER, prec=BF)
+    o = oracle_solve(b, iters, 0.7, mode=pp.MODE_PAPER)
+    assert_parity(g, o)
+
+
+def test_bf16x3_horizon_limit():
+    """The bf16 split shares the tensor-core kernels' horizon limit."""
+    P = pp.Projector(2, TC_MAX_H + 1, 0.02, workloads.base_bounds(2))
+    with pytest.raises(pp.PrismError) as e:
+        P.factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, BF)
+    assert e.value.status == 7
+    P.close()
+
+
+def test_bf16x3_plans_refuse_the_handle():
+    """A plan with a bf16-split handle fails at create (PRISM_ERR_UNSUPPORTED),
+    and the handle still solves."""
     import torch
     b = workloads.make_custom(31, 9, 4, 20, 0.05)
-    P = pp.Projector(4, 20, 0.05, b["bounds"])
-    with pytest.raises(pp.PrismError) as e:
-        P.factor(1.0, pp.MODE_PAPER, pp.SCALE_ROWNORM, BF)
-    assert e.value.status == 7
-    P.factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, BF)
+    P = pp.Projector(4, 20, 0.05, b["bounds"]).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, BF)
     xi, q0, v0 = to_dev(b)
     item = {"proj": P, "q0": q0, "v0": v0, "samples": xi, "out": torch.empty_like(xi),
             "primal": torch.empty((9, 4), device="cuda"), "dual": torch.empty((9, 4), device="cuda")}

@@ -300,8 +300,8 @@ def test_errors_are_reported_not_raised_on_device():
         P.solve(q0, v0, xi, 10, rho=2.0)
     assert e.value.status == 3
     with pytest.raises(pp.PrismError) as e:
-        P.factor(1.0, pp.MODE_PAPER, pp.SCALE_ROWNORM, pp.PREC_BF16X3)
-    assert e.value.status == 7
+        P.factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, 9)   # no such precision
+    assert e.value.status == 1
     P.factor(1.0)
     with pytest.raises(pp.PrismError) as e:
         P.solve(q0, v0, xi, -1)
