@@ -85,10 +85,8 @@ enum { PRISM_SCALE_ROWNORM = 0, PRISM_SCALE_NONE = 1 };
  * (prism_solve_opts), which use the split.  BF16X3 on the tensor cores in
  * bf16 (kind::f16 MMAs): both operands split exactly into three bf16 parts,
  * all products but the one of the two smallest parts, FP32 accumulation
- * (FP32-level accuracy); single solves (prism_proj_solve,
- * prism_proj_solve_ex, prism_proj_sample_solve, prism_proj_solve_host) in
- * either mode: plans with such a handle fail at create with
- * PRISM_ERR_UNSUPPORTED. */
+ * (FP32-level accuracy), in either mode, on every solve entry point and in
+ * plans (whose autotuner keeps such a group's K-apply). */
 enum { PRISM_PREC_FP32 = 0, PRISM_PREC_BF16X3 = 1, PRISM_PREC_TF32 = 2, PRISM_PREC_TF32X3 = 3 };
 
 #define PRISM_MAX_H 132   /* horizon limit of the on-chip solve kernel          */

@@ -3169,7 +3169,7 @@ struct Variant {
     // the ADMM tensor-core kernels that read warm-start inputs (x_init, dual_init);
     // the ones above do not (fewer registers)
     solve_fn admm_tc_w, b_admm_tc_w, admm_tc4_w, b_admm_tc4_w;
-    solve_fn admm_bf, paper_bf;   // the three-way bf16 split K-apply (one problem per launch)
+    solve_fn admm_bf, paper_bf, b_admm_bf, b_paper_bf;   // the three-way bf16 split K-apply
 };
 
 // The ADMM iteration with the tensor-core K-apply runs on solve_kernel_z; every
@@ -3182,7 +3182,8 @@ struct Variant {
      solve_kernel_z<HQv, 4, false, false>, solve_kernel_z<HQv, 4, true, false>,                               \
      solve_kernel_z<HQv, 8, false, true>, solve_kernel_z<HQv, 8, true, true>,                                 \
      solve_kernel_z<HQv, 4, false, true>, solve_kernel_z<HQv, 4, true, true>,                                 \
-     solve_kernel<HQv, PRISM_MODE_ADMM, true, false, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false, true>}
+     solve_kernel<HQv, PRISM_MODE_ADMM, true, false, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, false, true>, \
+     solve_kernel<HQv, PRISM_MODE_ADMM, true, true, true>, solve_kernel<HQv, PRISM_MODE_PAPER, true, true, true>}
 // prev_variant_hq (used for the rows that always exist) must list the same chunks.
 constexpr int kVariantHQ[] = {3, 5, 7, 9, 11, 13, 15, 17, 21, 25, 29, 33};
 constexpr bool variant_chain_ok()
@@ -3329,8 +3330,7 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
     const Variant *v = pick_variant(H);
     if (!v) return fail(PRISM_ERR_UNSUPPORTED, "H=%d exceeds the kernel limit", H);
     hq = v->hq;
-    if (bf && (batched || !tc))
-        return fail(PRISM_ERR_UNSUPPORTED, "the bf16 split K-apply runs solves of one problem per launch");
+    if (bf && !tc) return fail(PRISM_ERR_INVALID_ARG, "the bf16 split is a tensor-core K-apply");
     const bool z = tc && mode == PRISM_MODE_ADMM && !bf;
     if (z && nw == 0) nw = z_warps(v->hq);
     if (!z) nw = 8;
@@ -3343,7 +3343,7 @@ prism_status variant_config(int H, int mode, bool tc, bool batched, int n_max, i
                         : (batched ? solve_kernel_q8<13, true> : solve_kernel_q8<13, false>);
         smem = (size_t)solve_smem_q8(hq8).total;
     } else if (bf) {
-        fn = (mode == PRISM_MODE_ADMM) ? v->admm_bf : v->paper_bf;
+        fn = (mode == PRISM_MODE_ADMM) ? (batched ? v->b_admm_bf : v->admm_bf) : (batched ? v->b_paper_bf : v->paper_bf);
     } else if (!batched) {
         fn = (mode == PRISM_MODE_ADMM) ? (tc ? (nw == 4 ? (warm ? v->admm_tc4_w : v->admm_tc4)
                                                         : (warm ? v->admm_tc_w : v->admm_tc))
@@ -3423,6 +3423,7 @@ prism_status launch_config(prism_proj_t h, int batch, const Variant *&v, size_t 
 struct PlanGroup {
     int hq = 0, mode = 0;
     bool tc = false;
+    bool bf = false;                   // the three-way bf16 split K-apply (tc as well)
     bool warm = false;                 // some member starts from x_init / dual_init
     int nw = 8, threads = NTHREADS;    // warps and threads per block of the group's kernel
     std::vector<int> members;          // indices into the plan's problem list
@@ -4211,7 +4212,7 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
     pl->iters = iters;
     pl->flags = flags;
     prism_status st = PRISM_OK;
-    std::map<std::tuple<int, int, int>, int> index;   // (kernel class, mode, tc) -> group
+    std::map<std::tuple<int, int, int>, int> index;   // (kernel class, mode, K-apply: 0 FP32 pipe, 1 tf32, 2 bf16) -> group
     std::vector<SolveParams> all(nprob);
     std::vector<bool> use_tc(nprob);
     for (int k = 0; k < nprob && !st; ++k) {
@@ -4220,10 +4221,6 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
         st = prepare_solve(q.h, q.batch, q.q0, q.v0, q.samples, iters, q.h->rho, q.out, all[k]);
         if (st) break;
         if (q.h->device != dev) { st = fail(PRISM_ERR_INVALID_ARG, "problem %d: handle on another device", k); break; }
-        if (q.h->prec == PRISM_PREC_BF16X3) {
-            st = fail(PRISM_ERR_UNSUPPORTED, "problem %d: plans do not run the bf16 split K-apply", k);
-            break;
-        }
         all[k].primal = q.primal_res;
         all[k].dual = q.dual_res;
         all[k].x_init = q.x_init;
@@ -4231,10 +4228,11 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
         all[k].init_cm = 0;
         all[k].dual_out = q.dual_out;
         pl->num_sms = q.h->num_sms;
-        use_tc[k] = q.h->prec == PRISM_PREC_TF32X3 || q.h->prec == PRISM_PREC_TF32;
+        const bool bf = q.h->prec == PRISM_PREC_BF16X3;
+        use_tc[k] = q.h->prec == PRISM_PREC_TF32X3 || q.h->prec == PRISM_PREC_TF32 || bf;
         const Variant *v = pick_variant(q.h->H);
         if (!v) { st = fail(PRISM_ERR_UNSUPPORTED, "problem %d: H too large", k); break; }
-        const auto key = std::make_tuple(v->hq, q.h->mode, (int)use_tc[k]);
+        const auto key = std::make_tuple(v->hq, q.h->mode, (int)use_tc[k] + (int)bf);
         auto it = index.find(key);
         int gi;
         if (it == index.end()) {
@@ -4244,6 +4242,7 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             pl->groups[gi].hq = v->hq;
             pl->groups[gi].mode = q.h->mode;
             pl->groups[gi].tc = use_tc[k];
+            pl->groups[gi].bf = bf;
         } else {
             gi = it->second;
         }
@@ -4272,10 +4271,10 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             g.lp.MP_max = MP_max;
             int hq;
             st = variant_config(Hmax, g.mode, g.tc, true, n_max, MP_max, dev, 0, g.fn, g.threads, g.smem, g.bps, hq,
-                                g.warm);
+                                g.warm, g.bf);
             g.nw = g.threads / 32;
             g.hq = hq;
-            if (!st && g.tc && g.mode == PRISM_MODE_ADMM) {
+            if (!st && g.tc && !g.bf && g.mode == PRISM_MODE_ADMM) {
                 // the group's tiling (the members' own tiling choices do not apply to plans)
                 int t2 = 0;
                 for (SolveParams &sp : g.params) {
@@ -4334,7 +4333,8 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             bool can_switch = true;
             for (int k : g.members) {
                 const int prec = probs[k].h->prec;
-                if (prec == PRISM_PREC_TF32 || (!g.tc && !tc_fits(probs[k].h->H))) can_switch = false;
+                if (prec == PRISM_PREC_TF32 || prec == PRISM_PREC_BF16X3 || (!g.tc && !tc_fits(probs[k].h->H)))
+                    can_switch = false;
             }
             int Hmax = 2;
             for (int k : g.members) Hmax = std::max(Hmax, probs[k].h->H);
@@ -4347,7 +4347,7 @@ prism_status prism_plan_create(const prism_problem *probs, int nprob, int iters,
             for (int k : g.members)
                 all_q8 = all_q8 && probs[k].h->d_Khi8 != nullptr && probs[k].h->d_Klo8 != nullptr &&
                          q8_hq(probs[k].h->H) == q8_hq(Hmax);
-            if (g.tc && g.mode == PRISM_MODE_ADMM)
+            if (g.tc && !g.bf && g.mode == PRISM_MODE_ADMM)
                 for (int nw : {4, 8, 16})
                     if (nw != g.nw && (nw != 16 || (all_q8 && q8_hq(Hmax) > 0))) cands.push_back({true, nw});
             for (const auto &cd : cands) {

@@ -134,18 +134,43 @@ def test_bf16x3_horizon_limit():
     P.close()
 
 
-def test_bf16x3_plans_refuse_the_handle():
-    """A plan with a bf16-split handle fails at create (PRISM_ERR_UNSUPPORTED),
-    and the handle still solves."""
+@pytest.mark.parametrize("autotune,graph", [(False, False), (True, True)])
+def test_bf16x3_in_plans(autotune, graph):
+    """Plans with bf16-split handles (several kernel variants, both modes, a
+    ragged and an empty problem) next to split-TF32 and FP32 ones: each
+    problem's result equals its own single solve (the autotuner never moves a
+    bf16 group to another K-apply) and the oracle."""
     import torch
-    b = workloads.make_custom(31, 9, 4, 20, 0.05)
-    P = pp.Projector(4, 20, 0.05, b["bounds"]).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, BF)
-    xi, q0, v0 = to_dev(b)
-    item = {"proj": P, "q0": q0, "v0": v0, "samples": xi, "out": torch.empty_like(xi),
-            "primal": torch.empty((9, 4), device="cuda"), "dual": torch.empty((9, 4), device="cuda")}
-    with pytest.raises(pp.PrismError) as e:
-        pp.Plan([item], 30)
-    assert e.value.status == 7
-    g = _host(*P.solve(q0, v0, xi, 30))
-    assert_parity(g, oracle_solve(b, 30, 1.0), dual_tol=2e-4)
-    P.close()
+    shapes = [  # J, H, N, dt, mode, precision
+        (6, 20, 130, 0.05, pp.MODE_ADMM, BF), (7, 45, 77, 0.01, pp.MODE_ADMM, BF),
+        (12, 50, 300, 0.02, pp.MODE_ADMM, BF), (14, 64, 41, 0.02, pp.MODE_PAPER, BF),
+        (6, 97, 50, 0.02, pp.MODE_ADMM, BF), (7, 28, 0, 0.02, pp.MODE_ADMM, BF),
+        (12, 50, 64, 0.02, pp.MODE_ADMM, pp.PREC_TF32X3), (6, 20, 33, 0.05, pp.MODE_ADMM, pp.PREC_FP32)]
+    iters = 50
+    items, batches = [], []
+    for k, (J, H, N, dt, mode, prec) in enumerate(shapes):
+        b = workloads.make_custom(600 + 17 * k, N, J, H, dt, scale=0.9)
+        P = pp.Projector(J, H, dt, b["bounds"]).factor(1.0, mode, pp.SCALE_ROWNORM, prec)
+        items.append({"proj": P, "q0": torch.from_numpy(b["q0"]).cuda(), "v0": torch.from_numpy(b["v0"]).cuda(),
+                      "samples": torch.from_numpy(b["xi"]).cuda(),
+                      "out": torch.full((N, H, J), float("nan"), device="cuda"),
+                      "primal": torch.full((N, J), float("nan"), device="cuda"),
+                      "dual": torch.full((N, J), float("nan"), device="cuda")})
+        batches.append((b, mode))
+    plan = pp.Plan(items, iters, autotune=autotune, graph=graph)
+    plan.launch()
+    torch.cuda.synchronize()
+    for it, (b, mode), shape in zip(items, batches, shapes):
+        if shape[2] == 0:
+            continue
+        P = it["proj"]
+        x, pr, du = P.solve(it["q0"], it["v0"], it["samples"], iters)
+        torch.cuda.synchronize()
+        if shape[5] == BF:
+            assert float((it["out"] - x).abs().max()) <= 1e-6
+            assert float((it["primal"] - pr).abs().max()) <= 1e-6
+        g = _host(it["out"], it["primal"], it["dual"])
+        assert_parity(g, oracle_solve(b, iters, 1.0, mode=mode))
+    plan.close()
+    for it in items:
+        it["proj"].close()
