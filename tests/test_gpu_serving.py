@@ -18,6 +18,7 @@ CTRLS = {   # name: (J, H, N, dt, prec)
     "A": (12, 30, 64, 0.05, pp.PREC_FP32),
     "B": (6, 50, 500, 0.02, pp.PREC_FP32),
     "C": (14, 64, 200, 0.02, pp.PREC_TF32X3),
+    "D": (7, 45, 120, 0.02, pp.PREC_BF16X3),
 }
 ITERS = 80
 
@@ -66,17 +67,18 @@ def run_server(names, steps, interleave=True):
 
 def test_same_alone_and_in_the_mix():
     alone, _ = run_server(["A"], 3)
-    mix, st = run_server(["B", "A", "C"], 3)
+    mix, st = run_server(["B", "A", "C", "D"], 3)
     for k in range(3):
         assert np.array_equal(alone["A"][k], mix["A"][k]), k
-    assert st["completed"] == 9 and st["dropped"] == 0 and st["failed"] == 0
+    assert st["completed"] == 12 and st["dropped"] == 0 and st["failed"] == 0
 
 
-def test_server_equals_direct_warm_chain():
+@pytest.mark.parametrize("name", ["C", "D"])
+def test_server_equals_direct_warm_chain(name):
     import torch
-    outs, _ = run_server(["C"], 3, interleave=False)
-    J, H, N, dt, prec = CTRLS["C"]
-    d = controller_data("C", 3)
+    outs, _ = run_server([name], 3, interleave=False)
+    J, H, N, dt, prec = CTRLS[name]
+    d = controller_data(name, 3)
     P = pp.Projector(J, H, dt, d[0]["bounds"]).factor(1.0, pp.MODE_ADMM, pp.SCALE_ROWNORM, prec)
     state = None
     for k in range(3):
@@ -88,7 +90,7 @@ def test_server_equals_direct_warm_chain():
         x, _, _, new_state = P.solve_ex(q0, v0, xi, ITERS, dual_init=state, want_dual_out=True)
         state = new_state
         torch.cuda.synchronize()
-        assert np.array_equal(x.cpu().numpy(), outs["C"][k]), k
+        assert np.array_equal(x.cpu().numpy(), outs[name][k]), k
     P.close()
 
 
